@@ -1,0 +1,947 @@
+/*
+ * TREVR oracle: a plain, slow CPU restatement of the reverse ray tracer of
+ * Grond, Woods, Wadsley & Couchman (2019), "TREVR: A general N log^2 N
+ * radiative transfer algorithm" (arXiv:1902.08083).
+ *
+ * THIS IS TEST INFRASTRUCTURE. Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark load it. The product path (the CUDA
+ * library) shares no code with it and never calls it.
+ *
+ * Precision. Every value (cell moments, segment lengths, optical depths,
+ * fluxes) is computed in FP64. The discrete decisions of the method -- the
+ * Morton quantisation of a position, the opening-angle test (Eq. openangle),
+ * the refinement test (Eq. refcrit), "does the ray touch this cell" and the
+ * coincident-source skip -- are taken in IEEE fp32 with the operation
+ * sequences written out below, because those decisions turn floating point
+ * into integers and both implementations must take them in the same
+ * precision. The FP64 relative margin of each decision is recorded so a
+ * reader can see how close each call was.
+ *
+ * Build: gcc -O2 -fopenmp -ffp-contract=off -fPIC -shared (contraction must
+ * stay off so every fp32 expression rounds after each operation).
+ *
+ * Pins (tests/test_oracle_*.py): brute-force direct sum at theta=0 without
+ * absorption (Sec. 3.1.2: theta=0 is an O(N^2) ray trace); brute-force
+ * cell-by-cell optical depth at tau_ref<=0 (Sec. 2.2.3, full refinement);
+ * the uniform-medium closed form L exp(-alpha r)/(4 pi r^2) (Eqs. ient,
+ * simpint); an opaque occluder casts a shadow; hand-worked alpha_min /
+ * alpha_max and cell-density examples; tiling of space by the leaves.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define GRID_BITS 21
+#define GRID_MAX ((int32_t)1 << GRID_BITS) /* 2^21 cells per axis */
+#define ROOT 0                            /* preorder numbering: root first */
+#define MAXDEPTH 80
+
+enum {
+    ORC_OK = 0,
+    ORC_ERR_INVALID_ARGUMENT = 1,
+    ORC_ERR_OUT_OF_DOMAIN = 2,
+    ORC_ERR_NO_MEMORY = 6
+};
+
+/* ------------------------------------------------------------------------ */
+/* Tree held by the oracle.  Node numbering is preorder (lower child first). */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t n_gas, n_src, n_nodes, cap;
+    int bucket;
+    float lo32[3], side32, h32; /* domain as given (fp32) and cell size */
+    double lo[3], side, h;      /* the same in FP64 */
+
+    /* particles in Morton order */
+    uint64_t *key;
+    int64_t *perm;    /* perm[i] = caller index of the i-th sorted particle */
+    int64_t *rank;    /* rank[caller index] = sorted position */
+    int64_t *leaf_of; /* leaf node of the i-th sorted particle */
+    float *px, *py, *pz, *alpha, *w;
+
+    /* nodes */
+    int64_t *first, *count, *parent, *lower; /* lower child (upper = next subtree) */
+    int64_t *upper;
+    int32_t *split_bit, *depth; /* split_bit = -1 for a leaf */
+    int32_t (*glo)[3], (*ghi)[3];
+    double *W, *abar, (*amin_d)[3], (*amax_d)[3], *amin, *amax;
+    double *L, (*cen)[3], *lrad;
+    float *abar32, *dalpha32, *L32, (*cen32)[3], *l2_32;
+    float (*blo32)[3], (*bhi32)[3];
+    int64_t *src_first, *src_count; /* contiguous range in the sorted sources */
+
+    /* sources, sorted by (first particle of their leaf, caller index) */
+    int64_t *src_order, *src_leaf;
+    float *sx, *sy, *sz, *slum;
+} orc_tree;
+
+/* ------------------------------------------------------------------------ */
+/* Morton key: q_d = floor((x_d - lo_d) * (2^21/side)), clamped to 2^21-1,    */
+/* computed in fp32 (one subtraction and one multiplication, each rounded).   */
+/* Key bit 62 is x's top bit, then y, then z, down to bit 0 (z's bit 0).      */
+/* The tree is the binary tree of Morton prefixes: bisecting the longest axis */
+/* of a cube in x, y, z order (Sec. 2.3) is the Morton subdivision.           */
+/* ------------------------------------------------------------------------ */
+static int in_domain32(float x, float lo, float hi) { return x >= lo && x < hi; }
+
+static uint32_t quantize32(float x, float lo, float scale)
+{
+    float t = (x - lo) * scale;
+    uint32_t q = (uint32_t)t; /* t >= 0 by the domain check */
+    if (q > (uint32_t)(GRID_MAX - 1)) q = (uint32_t)(GRID_MAX - 1);
+    return q;
+}
+
+static uint64_t interleave3(uint32_t qx, uint32_t qy, uint32_t qz)
+{
+    uint64_t k = 0;
+    for (int b = GRID_BITS - 1; b >= 0; --b) {
+        k = (k << 1) | ((qx >> b) & 1u);
+        k = (k << 1) | ((qy >> b) & 1u);
+        k = (k << 1) | ((qz >> b) & 1u);
+    }
+    return k;
+}
+
+static uint32_t coord_of_key(uint64_t key, int axis)
+{
+    uint32_t g = 0;
+    for (int b = GRID_BITS - 1; b >= 0; --b) {
+        int pos = 3 * b + (2 - axis);
+        g = (g << 1) | (uint32_t)((key >> pos) & 1u);
+    }
+    return g;
+}
+
+static float domain_scale32(float side) { return 2097152.0f / side; }
+
+int orc_morton_keys(const float *x, const float *y, const float *z, int64_t n,
+                    const float lo[3], float side, uint64_t *keys)
+{
+    const float scale = domain_scale32(side);
+    float hi[3];
+    for (int d = 0; d < 3; ++d) hi[d] = lo[d] + side;
+    int bad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!in_domain32(x[i], lo[0], hi[0]) || !in_domain32(y[i], lo[1], hi[1]) ||
+            !in_domain32(z[i], lo[2], hi[2])) {
+            bad = 1;
+            keys[i] = 0;
+            continue;
+        }
+        keys[i] = interleave3(quantize32(x[i], lo[0], scale), quantize32(y[i], lo[1], scale),
+                              quantize32(z[i], lo[2], scale));
+    }
+    return bad ? ORC_ERR_OUT_OF_DOMAIN : ORC_OK;
+}
+
+/* Stable sort of (key, index): ties keep the caller's order. */
+typedef struct {
+    uint64_t key;
+    int64_t idx;
+} kv_t;
+
+static int kv_cmp(const void *a, const void *b)
+{
+    const kv_t *p = (const kv_t *)a, *q = (const kv_t *)b;
+    if (p->key < q->key) return -1;
+    if (p->key > q->key) return 1;
+    return (p->idx > q->idx) - (p->idx < q->idx);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Top-down tree.  A node over the sorted range [i, j) is a leaf when it      */
+/* holds at most N_B particles (the bucket, Sec. 2.2) or when all its keys    */
+/* are equal.  Otherwise it splits at the highest key bit b in which key[i]   */
+/* and key[j-1] differ: the lower child takes the particles whose bit b is 0. */
+/* The cut is a plane on axis (62-b) mod 3 at the middle of the Morton cell   */
+/* of the common prefix; the children are the parent box cut by that plane,  */
+/* so the leaves fill space (Sec. 2.2.2, 2.3).                                */
+/* ------------------------------------------------------------------------ */
+static int64_t build_rec(orc_tree *T, int64_t i, int64_t j, const int32_t glo[3],
+                         const int32_t ghi[3], int64_t parent, int32_t depth)
+{
+    int64_t id = T->n_nodes++;
+    T->first[id] = i;
+    T->count[id] = j - i;
+    T->parent[id] = parent;
+    T->depth[id] = depth;
+    for (int d = 0; d < 3; ++d) {
+        T->glo[id][d] = glo[d];
+        T->ghi[id][d] = ghi[d];
+    }
+    T->lower[id] = -1;
+    T->upper[id] = -1;
+    T->split_bit[id] = -1;
+    for (int64_t k = i; k < j; ++k) T->leaf_of[k] = id; /* overwritten by descendants */
+    if (j - i <= T->bucket || T->key[i] == T->key[j - 1]) return id;
+
+    uint64_t diff = T->key[i] ^ T->key[j - 1];
+    int b = 63;
+    while (!((diff >> b) & 1u)) --b;
+    int64_t k = i;
+    while (!((T->key[k] >> b) & 1u)) ++k; /* first particle of the upper side */
+    int axis = (62 - b) % 3;
+    int level = (62 - b) / 3;
+    int shift = GRID_BITS - 1 - level;
+    uint32_t g = coord_of_key(T->key[i], axis);
+    int32_t plane = (int32_t)(((g >> shift) | 1u) << shift);
+    T->split_bit[id] = b;
+
+    int32_t lo1[3], hi1[3], lo2[3], hi2[3];
+    for (int d = 0; d < 3; ++d) {
+        lo1[d] = lo2[d] = glo[d];
+        hi1[d] = hi2[d] = ghi[d];
+    }
+    hi1[axis] = plane;
+    lo2[axis] = plane;
+    T->lower[id] = build_rec(T, i, k, lo1, hi1, id, depth + 1);
+    T->upper[id] = build_rec(T, k, j, lo2, hi2, id, depth + 1);
+    return id;
+}
+
+static int split_axis_of(int32_t b) { return (62 - b) % 3; }
+
+/* fp32 world coordinate of grid plane g: lo + g*h, h = side * 2^-21. */
+static float world32(float lo, float h, int32_t g) { return lo + (float)g * h; }
+
+/* ------------------------------------------------------------------------ */
+/* Cell moments (Sec. 2.2.3, 2.3).                                           */
+/* ------------------------------------------------------------------------ */
+static void node_moments(orc_tree *T)
+{
+    const int64_t nn = T->n_nodes;
+    /* absorption: volume-weighted mean of alpha = kappa*rho, weight w = m/rho */
+    for (int64_t X = 0; X < nn; ++X) {
+        double sw = 0.0, swa = 0.0;
+        for (int64_t i = T->first[X]; i < T->first[X] + T->count[X]; ++i) {
+            sw += (double)T->w[i];
+            swa += (double)T->w[i] * (double)T->alpha[i];
+        }
+        T->W[X] = sw;
+        T->abar[X] = swa / sw;
+    }
+    /* directional alpha_min/alpha_max, children before parents (reverse preorder) */
+    for (int64_t X = nn - 1; X >= 0; --X) {
+        if (T->split_bit[X] < 0) {
+            for (int d = 0; d < 3; ++d) T->amin_d[X][d] = T->amax_d[X][d] = T->abar[X];
+        } else {
+            int64_t c1 = T->lower[X], c2 = T->upper[X];
+            int a = split_axis_of(T->split_bit[X]);
+            for (int d = 0; d < 3; ++d) {
+                if (d == a) {
+                    /* the ray crosses both children: optical depths add, then divide by width */
+                    double w1 = (double)(T->ghi[c1][d] - T->glo[c1][d]);
+                    double w2 = (double)(T->ghi[c2][d] - T->glo[c2][d]);
+                    double Wd = (double)(T->ghi[X][d] - T->glo[X][d]);
+                    T->amin_d[X][d] = (T->amin_d[c1][d] * w1 + T->amin_d[c2][d] * w2) / Wd;
+                    T->amax_d[X][d] = (T->amax_d[c1][d] * w1 + T->amax_d[c2][d] * w2) / Wd;
+                } else {
+                    /* the ray crosses one child or the other */
+                    T->amin_d[X][d] = fmin(T->amin_d[c1][d], T->amin_d[c2][d]);
+                    T->amax_d[X][d] = fmax(T->amax_d[c1][d], T->amax_d[c2][d]);
+                }
+            }
+        }
+        T->amin[X] = fmin(fmin(T->amin_d[X][0], T->amin_d[X][1]), T->amin_d[X][2]);
+        T->amax[X] = fmax(fmax(T->amax_d[X][0], T->amax_d[X][1]), T->amax_d[X][2]);
+    }
+    /* sources: total luminosity and centre of luminosity (Sec. 2.2.1) */
+    for (int64_t X = 0; X < nn; ++X) {
+        double sl = 0.0, sy[3] = {0.0, 0.0, 0.0};
+        for (int64_t s = T->src_first[X]; s < T->src_first[X] + T->src_count[X]; ++s) {
+            double Lj = (double)T->slum[s];
+            sl += Lj;
+            sy[0] += Lj * (double)T->sx[s];
+            sy[1] += Lj * (double)T->sy[s];
+            sy[2] += Lj * (double)T->sz[s];
+        }
+        T->L[X] = sl;
+        for (int d = 0; d < 3; ++d) T->cen[X][d] = sl > 0.0 ? sy[d] / sl : 0.0;
+    }
+    /* fp32 copies used by the decisions, and l = furthest vertex from the centroid */
+    for (int64_t X = 0; X < nn; ++X) {
+        T->abar32[X] = (float)T->abar[X];
+        T->dalpha32[X] = (float)(T->amax[X] - T->amin[X]);
+        T->L32[X] = (float)T->L[X];
+        for (int d = 0; d < 3; ++d) {
+            T->cen32[X][d] = (float)T->cen[X][d];
+            T->blo32[X][d] = world32(T->lo32[d], T->h32, T->glo[X][d]);
+            T->bhi32[X][d] = world32(T->lo32[d], T->h32, T->ghi[X][d]);
+        }
+        float l2 = 0.0f;
+        double l2d = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            float a = fmaxf(T->cen32[X][d] - T->blo32[X][d], T->bhi32[X][d] - T->cen32[X][d]);
+            l2 = l2 + a * a;
+            double lod = T->lo[d] + (double)T->glo[X][d] * T->h;
+            double hid = T->lo[d] + (double)T->ghi[X][d] * T->h;
+            double ad = fmax(T->cen[X][d] - lod, hid - T->cen[X][d]);
+            l2d += ad * ad;
+        }
+        T->l2_32[X] = l2;
+        T->lrad[X] = sqrt(l2d);
+    }
+}
+
+/* Descend from the root to the leaf whose box holds grid point g. */
+static int64_t leaf_of_point(const orc_tree *T, const uint32_t g[3])
+{
+    int64_t X = ROOT;
+    while (T->split_bit[X] >= 0) {
+        int a = split_axis_of(T->split_bit[X]);
+        int64_t up = T->upper[X];
+        X = ((int32_t)g[a] >= T->glo[up][a]) ? up : T->lower[X];
+    }
+    return X;
+}
+
+static int64_t lower_bound_i64(const int64_t *a, int64_t n, int64_t v)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t m = lo + (hi - lo) / 2;
+        if (a[m] < v) lo = m + 1;
+        else hi = m;
+    }
+    return lo;
+}
+
+void orc_tree_free(orc_tree *T);
+
+#define ALLOC(ptr, n) \
+    do { \
+        (ptr) = calloc((size_t)((n) > 0 ? (n) : 1), sizeof(*(ptr))); \
+        if (!(ptr)) goto nomem; \
+    } while (0)
+
+/*
+ * Build the oracle's tree.  gas_x/y/z, alpha, weight (NULL = all 1) have
+ * n_gas entries in the caller's order; src_* have n_src entries.
+ */
+int orc_build(const float *gas_x, const float *gas_y, const float *gas_z, const float *alpha,
+              const float *weight, int64_t n_gas, const float *src_x, const float *src_y,
+              const float *src_z, const float *src_lum, int64_t n_src, const float lo[3],
+              float side, int bucket, orc_tree **out)
+{
+    *out = NULL;
+    if (n_gas <= 0 || n_src < 0 || bucket < 1 || !(side > 0.0f) || !isfinite(side))
+        return ORC_ERR_INVALID_ARGUMENT;
+    for (int64_t i = 0; i < n_gas; ++i) {
+        if (!isfinite(alpha[i]) || alpha[i] < 0.0f) return ORC_ERR_INVALID_ARGUMENT;
+        if (weight && (!isfinite(weight[i]) || !(weight[i] > 0.0f))) return ORC_ERR_INVALID_ARGUMENT;
+    }
+    for (int64_t s = 0; s < n_src; ++s)
+        if (!isfinite(src_lum[s]) || src_lum[s] < 0.0f) return ORC_ERR_INVALID_ARGUMENT;
+
+    orc_tree *T = calloc(1, sizeof(orc_tree));
+    if (!T) return ORC_ERR_NO_MEMORY;
+    T->n_gas = n_gas;
+    T->n_src = n_src;
+    T->bucket = bucket;
+    T->side32 = side;
+    T->h32 = side * (1.0f / 2097152.0f);
+    T->side = (double)side;
+    T->h = (double)side / 2097152.0;
+    for (int d = 0; d < 3; ++d) {
+        T->lo32[d] = lo[d];
+        T->lo[d] = (double)lo[d];
+    }
+    int64_t cap = 2 * n_gas;
+    T->cap = cap;
+    ALLOC(T->key, n_gas);
+    ALLOC(T->perm, n_gas);
+    ALLOC(T->rank, n_gas);
+    ALLOC(T->leaf_of, n_gas);
+    ALLOC(T->px, n_gas);
+    ALLOC(T->py, n_gas);
+    ALLOC(T->pz, n_gas);
+    ALLOC(T->alpha, n_gas);
+    ALLOC(T->w, n_gas);
+    ALLOC(T->first, cap);
+    ALLOC(T->count, cap);
+    ALLOC(T->parent, cap);
+    ALLOC(T->lower, cap);
+    ALLOC(T->upper, cap);
+    ALLOC(T->split_bit, cap);
+    ALLOC(T->depth, cap);
+    ALLOC(T->glo, cap);
+    ALLOC(T->ghi, cap);
+    ALLOC(T->W, cap);
+    ALLOC(T->abar, cap);
+    ALLOC(T->amin_d, cap);
+    ALLOC(T->amax_d, cap);
+    ALLOC(T->amin, cap);
+    ALLOC(T->amax, cap);
+    ALLOC(T->L, cap);
+    ALLOC(T->cen, cap);
+    ALLOC(T->lrad, cap);
+    ALLOC(T->abar32, cap);
+    ALLOC(T->dalpha32, cap);
+    ALLOC(T->L32, cap);
+    ALLOC(T->cen32, cap);
+    ALLOC(T->l2_32, cap);
+    ALLOC(T->blo32, cap);
+    ALLOC(T->bhi32, cap);
+    ALLOC(T->src_first, cap);
+    ALLOC(T->src_count, cap);
+    ALLOC(T->src_order, n_src);
+    ALLOC(T->src_leaf, n_src);
+    ALLOC(T->sx, n_src);
+    ALLOC(T->sy, n_src);
+    ALLOC(T->sz, n_src);
+    ALLOC(T->slum, n_src);
+
+    {
+        uint64_t *k0 = malloc((size_t)n_gas * sizeof(uint64_t));
+        kv_t *kv = malloc((size_t)n_gas * sizeof(kv_t));
+        if (!k0 || !kv) {
+            free(k0);
+            free(kv);
+            goto nomem;
+        }
+        int rc = orc_morton_keys(gas_x, gas_y, gas_z, n_gas, lo, side, k0);
+        if (rc != ORC_OK) {
+            free(k0);
+            free(kv);
+            orc_tree_free(T);
+            return rc;
+        }
+        for (int64_t i = 0; i < n_gas; ++i) {
+            kv[i].key = k0[i];
+            kv[i].idx = i;
+        }
+        qsort(kv, (size_t)n_gas, sizeof(kv_t), kv_cmp);
+        for (int64_t i = 0; i < n_gas; ++i) {
+            int64_t o = kv[i].idx;
+            T->key[i] = kv[i].key;
+            T->perm[i] = o;
+            T->rank[o] = i;
+            T->px[i] = gas_x[o];
+            T->py[i] = gas_y[o];
+            T->pz[i] = gas_z[o];
+            T->alpha[i] = alpha[o];
+            T->w[i] = weight ? weight[o] : 1.0f;
+        }
+        free(k0);
+        free(kv);
+    }
+
+    {
+        int32_t glo[3] = {0, 0, 0}, ghi[3] = {GRID_MAX, GRID_MAX, GRID_MAX};
+        T->n_nodes = 0;
+        build_rec(T, 0, n_gas, glo, ghi, -1, 0);
+    }
+
+    /* sources: quantise like particles, descend to their leaf, sort by
+       (first particle of the leaf, caller index) */
+    if (n_src > 0) {
+        const float scale = domain_scale32(side);
+        float hi[3];
+        for (int d = 0; d < 3; ++d) hi[d] = lo[d] + side;
+        kv_t *kv = malloc((size_t)n_src * sizeof(kv_t));
+        int64_t *leaf0 = malloc((size_t)n_src * sizeof(int64_t));
+        if (!kv || !leaf0) {
+            free(kv);
+            free(leaf0);
+            goto nomem;
+        }
+        for (int64_t s = 0; s < n_src; ++s) {
+            if (!in_domain32(src_x[s], lo[0], hi[0]) || !in_domain32(src_y[s], lo[1], hi[1]) ||
+                !in_domain32(src_z[s], lo[2], hi[2])) {
+                free(kv);
+                free(leaf0);
+                orc_tree_free(T);
+                return ORC_ERR_OUT_OF_DOMAIN;
+            }
+            uint32_t g[3] = {quantize32(src_x[s], lo[0], scale), quantize32(src_y[s], lo[1], scale),
+                             quantize32(src_z[s], lo[2], scale)};
+            leaf0[s] = leaf_of_point(T, g);
+            kv[s].key = (uint64_t)T->first[leaf0[s]];
+            kv[s].idx = s;
+        }
+        qsort(kv, (size_t)n_src, sizeof(kv_t), kv_cmp);
+        for (int64_t s = 0; s < n_src; ++s) {
+            int64_t o = kv[s].idx;
+            T->src_order[s] = o;
+            T->src_leaf[s] = leaf0[o];
+            T->sx[s] = src_x[o];
+            T->sy[s] = src_y[o];
+            T->sz[s] = src_z[o];
+            T->slum[s] = src_lum[o];
+        }
+        free(kv);
+        free(leaf0);
+    }
+    {
+        /* source range of each node: sources whose leaf starts inside the node's particle range */
+        int64_t *lf = malloc((size_t)(n_src > 0 ? n_src : 1) * sizeof(int64_t));
+        if (!lf) goto nomem;
+        for (int64_t s = 0; s < n_src; ++s) lf[s] = T->first[T->src_leaf[s]];
+        for (int64_t X = 0; X < T->n_nodes; ++X) {
+            int64_t a = lower_bound_i64(lf, n_src, T->first[X]);
+            int64_t b = lower_bound_i64(lf, n_src, T->first[X] + T->count[X]);
+            T->src_first[X] = a;
+            T->src_count[X] = b - a;
+        }
+        free(lf);
+    }
+    node_moments(T);
+    *out = T;
+    return ORC_OK;
+nomem:
+    orc_tree_free(T);
+    return ORC_ERR_NO_MEMORY;
+}
+
+void orc_tree_free(orc_tree *T)
+{
+    if (!T) return;
+    void *ptrs[] = {T->key, T->perm, T->rank, T->leaf_of, T->px, T->py, T->pz, T->alpha, T->w,
+                    T->first, T->count, T->parent, T->lower, T->upper, T->split_bit, T->depth,
+                    T->glo, T->ghi, T->W, T->abar, T->amin_d, T->amax_d, T->amin, T->amax, T->L,
+                    T->cen, T->lrad, T->abar32, T->dalpha32, T->L32, T->cen32, T->l2_32, T->blo32,
+                    T->bhi32, T->src_first, T->src_count, T->src_order, T->src_leaf, T->sx, T->sy,
+                    T->sz, T->slum};
+    for (size_t k = 0; k < sizeof(ptrs) / sizeof(ptrs[0]); ++k) free(ptrs[k]);
+    free(T);
+}
+
+int64_t orc_n_nodes(const orc_tree *T) { return T->n_nodes; }
+
+/* Copy the tree out (caller allocates n_nodes / n_gas / n_src sized arrays; any may be NULL). */
+void orc_export_nodes(const orc_tree *T, int64_t *first, int64_t *count, int64_t *parent,
+                      int64_t *lower, int64_t *upper, int32_t *split_bit, int32_t *depth,
+                      int32_t *glo, int32_t *ghi, double *W, double *abar, double *amin,
+                      double *amax, double *L, double *cen, double *lrad, int64_t *src_first,
+                      int64_t *src_count)
+{
+    for (int64_t X = 0; X < T->n_nodes; ++X) {
+        if (first) first[X] = T->first[X];
+        if (count) count[X] = T->count[X];
+        if (parent) parent[X] = T->parent[X];
+        if (lower) lower[X] = T->lower[X];
+        if (upper) upper[X] = T->upper[X];
+        if (split_bit) split_bit[X] = T->split_bit[X];
+        if (depth) depth[X] = T->depth[X];
+        for (int d = 0; d < 3; ++d) {
+            if (glo) glo[3 * X + d] = T->glo[X][d];
+            if (ghi) ghi[3 * X + d] = T->ghi[X][d];
+            if (cen) cen[3 * X + d] = T->cen[X][d];
+        }
+        if (W) W[X] = T->W[X];
+        if (abar) abar[X] = T->abar[X];
+        if (amin) amin[X] = T->amin[X];
+        if (amax) amax[X] = T->amax[X];
+        if (L) L[X] = T->L[X];
+        if (lrad) lrad[X] = T->lrad[X];
+        if (src_first) src_first[X] = T->src_first[X];
+        if (src_count) src_count[X] = T->src_count[X];
+    }
+}
+
+/* fp32 node values the decisions use. */
+void orc_export_nodes32(const orc_tree *T, float *abar32, float *dalpha32, float *L32,
+                        float *cen32, float *l2_32, float *blo32, float *bhi32)
+{
+    for (int64_t X = 0; X < T->n_nodes; ++X) {
+        if (abar32) abar32[X] = T->abar32[X];
+        if (dalpha32) dalpha32[X] = T->dalpha32[X];
+        if (L32) L32[X] = T->L32[X];
+        if (l2_32) l2_32[X] = T->l2_32[X];
+        for (int d = 0; d < 3; ++d) {
+            if (cen32) cen32[3 * X + d] = T->cen32[X][d];
+            if (blo32) blo32[3 * X + d] = T->blo32[X][d];
+            if (bhi32) bhi32[3 * X + d] = T->bhi32[X][d];
+        }
+    }
+}
+
+/* Directional alpha_min / alpha_max (x, y, z) of every node. */
+void orc_export_directional(const orc_tree *T, double *amin_d, double *amax_d)
+{
+    for (int64_t X = 0; X < T->n_nodes; ++X)
+        for (int d = 0; d < 3; ++d) {
+            amin_d[3 * X + d] = T->amin_d[X][d];
+            amax_d[3 * X + d] = T->amax_d[X][d];
+        }
+}
+
+void orc_export_particles(const orc_tree *T, uint64_t *key, int64_t *perm, int64_t *leaf_of)
+{
+    for (int64_t i = 0; i < T->n_gas; ++i) {
+        if (key) key[i] = T->key[i];
+        if (perm) perm[i] = T->perm[i];
+        if (leaf_of) leaf_of[i] = T->leaf_of[i];
+    }
+}
+
+void orc_export_sources(const orc_tree *T, int64_t *src_order, int64_t *src_leaf)
+{
+    for (int64_t s = 0; s < T->n_src; ++s) {
+        if (src_order) src_order[s] = T->src_order[s];
+        if (src_leaf) src_leaf[s] = T->src_leaf[s];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reverse ray (Sec. 2.2.2-2.2.3).                                           */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    /* fp32 ray for the decisions */
+    float p[3], d[3], inv[3], len;
+    /* FP64 ray for the values */
+    double P[3], D[3], LEN;
+} ray_t;
+
+typedef struct {
+    double sum, comp; /* Neumaier summation */
+} nsum_t;
+
+static void nsum_add(nsum_t *s, double x)
+{
+    double t = s->sum + x;
+    if (fabs(s->sum) >= fabs(x)) s->comp += (s->sum - t) + x;
+    else s->comp += (x - t) + s->sum;
+    s->sum = t;
+}
+static double nsum_get(const nsum_t *s) { return s->sum + s->comp; }
+
+typedef struct {
+    int64_t interactions, segments, visited, refinements;
+    double margin;
+    /* optional record of the frozen decisions */
+    int record;
+} counters_t;
+
+static void note_margin(counters_t *c, double m)
+{
+    if (m < c->margin) c->margin = m;
+}
+
+/* fp32 length of the ray inside the node box (slab method); 0 if it misses. */
+static float clip32(const ray_t *R, const float blo[3], const float bhi[3])
+{
+    float t0 = 0.0f, t1 = 1.0f;
+    for (int k = 0; k < 3; ++k) {
+        if (R->d[k] != 0.0f) {
+            float ta = (blo[k] - R->p[k]) * R->inv[k];
+            float tb = (bhi[k] - R->p[k]) * R->inv[k];
+            t0 = fmaxf(t0, fminf(ta, tb));
+            t1 = fminf(t1, fmaxf(ta, tb));
+        } else if (R->p[k] < blo[k] || R->p[k] > bhi[k]) {
+            return 0.0f;
+        }
+    }
+    return t1 > t0 ? (t1 - t0) * R->len : 0.0f;
+}
+
+/* FP64 length of the ray inside the node box. */
+static double clip64(const orc_tree *T, const ray_t *R, int64_t X)
+{
+    double t0 = 0.0, t1 = 1.0;
+    for (int k = 0; k < 3; ++k) {
+        double lo = T->lo[k] + (double)T->glo[X][k] * T->h;
+        double hi = T->lo[k] + (double)T->ghi[X][k] * T->h;
+        if (R->D[k] != 0.0) {
+            double ta = (lo - R->P[k]) / R->D[k];
+            double tb = (hi - R->P[k]) / R->D[k];
+            t0 = fmax(t0, fmin(ta, tb));
+            t1 = fmin(t1, fmax(ta, tb));
+        } else if (R->P[k] < lo || R->P[k] > hi) {
+            return 0.0;
+        }
+    }
+    return t1 > t0 ? (t1 - t0) * R->LEN : 0.0;
+}
+
+typedef struct {
+    nsum_t tau;
+    double len_sum; /* sum of the FP64 lengths of the used segments (tiling check) */
+    int64_t nseg;
+} raysum_t;
+
+/* Optical depth through node X: use its mean absorption unless the
+   refinement criterion (Eq. refcrit, fp32) asks for its children. */
+static void seg(const orc_tree *T, const ray_t *R, int64_t X, float tau_ref, counters_t *c,
+                raysum_t *rs)
+{
+    float l32 = clip32(R, T->blo32[X], T->bhi32[X]);
+    if (!(l32 > 0.0f)) return;
+    if (T->split_bit[X] >= 0) {
+        int refine = (tau_ref <= 0.0f) || (T->dalpha32[X] * l32 > tau_ref);
+        if (tau_ref > 0.0f) {
+            double crit = (T->amax[X] - T->amin[X]) * clip64(T, R, X);
+            note_margin(c, fabs(crit - (double)tau_ref) / (double)tau_ref);
+        }
+        if (refine) {
+            c->refinements++;
+            seg(T, R, T->lower[X], tau_ref, c, rs);
+            seg(T, R, T->upper[X], tau_ref, c, rs);
+            return;
+        }
+    }
+    double l64 = clip64(T, R, X);
+    nsum_add(&rs->tau, T->abar[X] * l64);
+    rs->len_sum += l64;
+    rs->nseg++;
+    c->segments++;
+}
+
+static int64_t sibling_of(const orc_tree *T, int64_t U)
+{
+    int64_t P = T->parent[U];
+    return T->lower[P] == U ? T->upper[P] : T->lower[P];
+}
+
+/*
+ * Optical depth from the sink (in leaf S) to the point q (in node C).  The
+ * segments are S, C, and the siblings of the nodes on the two paths up to
+ * (not including) the children of their lowest common ancestor A: these
+ * boxes tile box A, which holds the whole ray (Sec. 3.1.3: the walk goes up
+ * from the sink's bucket and from the source cell).
+ */
+static void ray_tau(const orc_tree *T, const ray_t *R, int64_t S, int64_t C, float tau_ref,
+                    counters_t *c, raysum_t *rs)
+{
+    seg(T, R, S, tau_ref, c, rs);
+    if (S == C) return;
+    seg(T, R, C, tau_ref, c, rs);
+    int64_t u = S, v = C;
+    while (T->depth[u] > T->depth[v]) {
+        seg(T, R, sibling_of(T, u), tau_ref, c, rs);
+        u = T->parent[u];
+    }
+    while (T->depth[v] > T->depth[u]) {
+        seg(T, R, sibling_of(T, v), tau_ref, c, rs);
+        v = T->parent[v];
+    }
+    while (T->parent[u] != T->parent[v]) {
+        seg(T, R, sibling_of(T, u), tau_ref, c, rs);
+        seg(T, R, sibling_of(T, v), tau_ref, c, rs);
+        u = T->parent[u];
+        v = T->parent[v];
+    }
+}
+
+typedef struct {
+    int64_t node;  /* C */
+    double q[3];   /* pseudo-source position */
+    double L;      /* luminosity */
+    double tau;    /* optical depth along the ray */
+    double len_sum;
+    double flux;   /* contribution */
+    int64_t nseg;
+    int64_t src;   /* sorted source index, or -1 for a merged node */
+} inter_t;
+
+typedef struct {
+    inter_t *buf;
+    int64_t n, cap;
+} inter_log_t;
+
+/* One pseudo-source (L at q, inside node C) seen from sorted particle i. */
+static double contribute(const orc_tree *T, int64_t i, int64_t S, int64_t C, const float q32[3],
+                         const double q64[3], double L, float tau_ref, float smin2,
+                         counters_t *c, inter_log_t *log, int64_t src)
+{
+    ray_t R;
+    R.p[0] = T->px[i];
+    R.p[1] = T->py[i];
+    R.p[2] = T->pz[i];
+    for (int k = 0; k < 3; ++k) {
+        R.d[k] = q32[k] - R.p[k];
+        R.inv[k] = R.d[k] != 0.0f ? 1.0f / R.d[k] : 0.0f;
+        R.P[k] = (double)R.p[k];
+        R.D[k] = q64[k] - R.P[k];
+    }
+    float s2 = R.d[0] * R.d[0] + R.d[1] * R.d[1] + R.d[2] * R.d[2];
+    if (s2 < smin2) return 0.0; /* a source on top of the sink adds nothing */
+    R.len = sqrtf(s2);
+    double S2 = R.D[0] * R.D[0] + R.D[1] * R.D[1] + R.D[2] * R.D[2];
+    R.LEN = sqrt(S2);
+    raysum_t rs;
+    memset(&rs, 0, sizeof(rs));
+    ray_tau(T, &R, S, C, tau_ref, c, &rs);
+    double tau = nsum_get(&rs.tau);
+    /* Eq. simpint: I = L exp(-tau) / (4 pi s^2) */
+    double f = L * exp(-tau) / (4.0 * M_PI * S2);
+    c->interactions++;
+    if (log && log->n < log->cap) {
+        inter_t *e = &log->buf[log->n];
+        e->node = C;
+        for (int k = 0; k < 3; ++k) e->q[k] = q64[k];
+        e->L = L;
+        e->tau = tau;
+        e->len_sum = rs.len_sum;
+        e->flux = f;
+        e->nseg = rs.nseg;
+        e->src = src;
+    }
+    if (log) log->n++;
+    return f;
+}
+
+/*
+ * Source walk for the sink at sorted position i (Sec. 2.2.1): a node whose
+ * cell satisfies the opening-angle criterion theta > l/r (Eq. openangle)
+ * acts as one source of luminosity L_X at its centre of luminosity;
+ * otherwise it is opened; a leaf that is opened contributes its sources one
+ * by one.  fp32 decision: l^2 < theta^2 r^2.
+ */
+static double sink_flux(const orc_tree *T, int64_t i, float theta, float tau_ref,
+                        counters_t *c, inter_log_t *log)
+{
+    const float theta2 = theta * theta;
+    const float smin = 1e-12f * T->side32;
+    const float smin2 = smin * smin;
+    const float p[3] = {T->px[i], T->py[i], T->pz[i]};
+    const int64_t S = T->leaf_of[i];
+    nsum_t F = {0.0, 0.0};
+    int64_t stack[MAXDEPTH + 2];
+    int sp = 0;
+    stack[sp++] = ROOT;
+    while (sp > 0) {
+        int64_t X = stack[--sp];
+        if (!(T->L[X] > 0.0)) continue;
+        c->visited++;
+        float r2 = 0.0f;
+        double r2d = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            float e = fmaxf(fmaxf(T->blo32[X][d] - p[d], p[d] - T->bhi32[X][d]), 0.0f);
+            r2 = r2 + e * e;
+            double lod = T->lo[d] + (double)T->glo[X][d] * T->h;
+            double hid = T->lo[d] + (double)T->ghi[X][d] * T->h;
+            double ed = fmax(fmax(lod - (double)p[d], (double)p[d] - hid), 0.0);
+            r2d += ed * ed;
+        }
+        int accept = T->l2_32[X] < theta2 * r2;
+        {
+            double tr = (double)theta * sqrt(r2d), l = T->lrad[X];
+            double den = fmax(tr, l);
+            if (den > 0.0) note_margin(c, fabs(l - tr) / den);
+        }
+        if (accept) {
+            nsum_add(&F, contribute(T, i, S, X, T->cen32[X], T->cen[X], T->L[X], tau_ref, smin2, c,
+                                    log, -1));
+        } else if (T->split_bit[X] < 0) {
+            for (int64_t s = T->src_first[X]; s < T->src_first[X] + T->src_count[X]; ++s) {
+                if (!(T->slum[s] > 0.0f)) continue;
+                const float q32[3] = {T->sx[s], T->sy[s], T->sz[s]};
+                const double q64[3] = {(double)T->sx[s], (double)T->sy[s], (double)T->sz[s]};
+                nsum_add(&F, contribute(T, i, S, X, q32, q64, (double)T->slum[s], tau_ref, smin2,
+                                        c, log, s));
+            }
+        } else {
+            stack[sp++] = T->upper[X];
+            stack[sp++] = T->lower[X];
+        }
+    }
+    return nsum_get(&F);
+}
+
+/*
+ * Flux (Eq. simpint summed over pseudo-sources) for the sinks given by their
+ * caller indices.  counters (nullable) gets 4 int64 per sink: interactions,
+ * segments, visited source nodes, refinements.  margin (nullable) gets the
+ * smallest FP64 relative margin of any decision taken for that sink.
+ */
+int orc_flux(const orc_tree *T, const int64_t *sinks, int64_t n_sink, float theta, float tau_ref,
+             double *flux, int64_t *counters, double *margin, int nthreads)
+{
+    if (!(theta >= 0.0f) || !isfinite(theta) || isnan(tau_ref)) return ORC_ERR_INVALID_ARGUMENT;
+    for (int64_t k = 0; k < n_sink; ++k)
+        if (sinks[k] < 0 || sinks[k] >= T->n_gas) return ORC_ERR_INVALID_ARGUMENT;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t k = 0; k < n_sink; ++k) {
+        counters_t c;
+        memset(&c, 0, sizeof(c));
+        c.margin = INFINITY;
+        int64_t i = T->rank[sinks[k]];
+        flux[k] = sink_flux(T, i, theta, tau_ref, &c, NULL);
+        if (counters) {
+            counters[4 * k + 0] = c.interactions;
+            counters[4 * k + 1] = c.segments;
+            counters[4 * k + 2] = c.visited;
+            counters[4 * k + 3] = c.refinements;
+        }
+        if (margin) margin[k] = c.margin;
+    }
+    return ORC_OK;
+}
+
+/* Interaction list of one sink (caller index): returns the number of
+   interactions; fills at most cap entries. */
+int64_t orc_sink_interactions(const orc_tree *T, int64_t sink, float theta, float tau_ref,
+                              int64_t cap, int64_t *node, double *q, double *L, double *tau,
+                              double *len_sum, double *flux, int64_t *nseg, int64_t *src)
+{
+    inter_log_t log;
+    log.n = 0;
+    log.cap = cap;
+    log.buf = cap > 0 ? calloc((size_t)cap, sizeof(inter_t)) : NULL;
+    if (cap > 0 && !log.buf) return -1;
+    counters_t c;
+    memset(&c, 0, sizeof(c));
+    c.margin = INFINITY;
+    sink_flux(T, T->rank[sink], theta, tau_ref, &c, &log);
+    for (int64_t k = 0; k < log.n && k < cap; ++k) {
+        const inter_t *e = &log.buf[k];
+        if (node) node[k] = e->node;
+        if (q)
+            for (int d = 0; d < 3; ++d) q[3 * k + d] = e->q[d];
+        if (L) L[k] = e->L;
+        if (tau) tau[k] = e->tau;
+        if (len_sum) len_sum[k] = e->len_sum;
+        if (flux) flux[k] = e->flux;
+        if (nseg) nseg[k] = e->nseg;
+        if (src) src[k] = e->src;
+    }
+    free(log.buf);
+    return log.n;
+}
+
+/* Optical depth of the ray from sorted particle (caller index) sink to the
+   point q inside node C, with the segment set of the method. */
+double orc_ray_tau(const orc_tree *T, int64_t sink, int64_t C, const float q[3], float tau_ref,
+                   double *len_sum, int64_t *nseg)
+{
+    int64_t i = T->rank[sink];
+    ray_t R;
+    R.p[0] = T->px[i];
+    R.p[1] = T->py[i];
+    R.p[2] = T->pz[i];
+    for (int k = 0; k < 3; ++k) {
+        R.d[k] = q[k] - R.p[k];
+        R.inv[k] = R.d[k] != 0.0f ? 1.0f / R.d[k] : 0.0f;
+        R.P[k] = (double)R.p[k];
+        R.D[k] = (double)q[k] - R.P[k];
+    }
+    R.len = sqrtf(R.d[0] * R.d[0] + R.d[1] * R.d[1] + R.d[2] * R.d[2]);
+    R.LEN = sqrt(R.D[0] * R.D[0] + R.D[1] * R.D[1] + R.D[2] * R.D[2]);
+    counters_t c;
+    memset(&c, 0, sizeof(c));
+    c.margin = INFINITY;
+    raysum_t rs;
+    memset(&rs, 0, sizeof(rs));
+    ray_tau(T, &R, T->leaf_of[i], C, tau_ref, &c, &rs);
+    if (len_sum) *len_sum = rs.len_sum;
+    if (nseg) *nseg = rs.nseg;
+    return nsum_get(&rs.tau);
+}
+
+/* Leaf holding the grid point of (x,y,z) (same quantisation as the keys). */
+int64_t orc_leaf_of_point(const orc_tree *T, float x, float y, float z)
+{
+    const float scale = domain_scale32(T->side32);
+    uint32_t g[3] = {quantize32(x, T->lo32[0], scale), quantize32(y, T->lo32[1], scale),
+                     quantize32(z, T->lo32[2], scale)};
+    return leaf_of_point(T, g);
+}

@@ -1,0 +1,229 @@
+"""Pins for the oracle's source walk, reverse ray and flux sum.
+
+Fixed by: the brute-force direct sum at theta=0 without absorption
+(Sec. 3.1.2: theta=0 is an O(N^2) ray trace), a brute-force cell-by-cell
+optical depth through every leaf at tau_ref<=0 (full refinement, Sec. 3.1.4),
+the tiling of a ray by the method's segments (Sec. 2.2.2: the tree fills
+space), the uniform-medium closed form L exp(-alpha r)/(4 pi r^2) (Eqs. ient
+and simpint), the partition of the sources by the opening-angle walk
+(Eq. openangle), a shadow behind an opaque occluder (Sec. 3.2), and the
+paper's statement that the error stays below tau_ref (Eq. reffrac, Sec. 3.1.3).
+"""
+import numpy as np
+import pytest
+
+import workloads
+
+G = 1 << 21
+
+
+def _tree(oracle_lib, P, **kw):
+    return oracle_lib.OracleTree(P["gas_xyz"], P["alpha"], P["src_xyz"], P["src_lum"],
+                                 bucket=P["bucket"], weight=P.get("weight"), **kw)
+
+
+def _leaf_boxes(T):
+    N = T.nodes()
+    leaf = np.nonzero(N["split_bit"] < 0)[0]
+    h = T.side / G
+    lo = T.lo + N["glo"][leaf] * h
+    hi = T.lo + N["ghi"][leaf] * h
+    return lo, hi, N["abar"][leaf]
+
+
+def _clip_all(lo, hi, p, q):
+    """FP64 length of the segment p->q inside every box (vectorised slab test)."""
+    d = q - p
+    t0 = np.zeros(len(lo))
+    t1 = np.ones(len(lo))
+    for k in range(3):
+        if d[k] != 0.0:
+            ta = (lo[:, k] - p[k]) / d[k]
+            tb = (hi[:, k] - p[k]) / d[k]
+            t0 = np.maximum(t0, np.minimum(ta, tb))
+            t1 = np.minimum(t1, np.maximum(ta, tb))
+        else:
+            out = (p[k] < lo[:, k]) | (p[k] > hi[:, k])
+            t1 = np.where(out, -1.0, t1)
+    return np.maximum(t1 - t0, 0.0) * np.linalg.norm(d)
+
+
+def test_theta0_no_absorption_is_direct_sum(oracle_lib):
+    P = workloads.uniform_box(n_gas=1500, n_src=50, seed=2, alpha=0.0)
+    T = _tree(oracle_lib, P)
+    sinks = np.arange(0, 1500, 3)
+    f, cnt, _ = T.flux(0.0, 0.1, sinks=sinks, with_counters=True)
+    p = P["gas_xyz"][:, sinks].astype(np.float64)
+    y = P["src_xyz"].astype(np.float64)
+    L = P["src_lum"].astype(np.float64)
+    r2 = ((p[:, :, None] - y[:, None, :]) ** 2).sum(0)
+    ref = (L[None, :] / (4 * np.pi * r2)).sum(1)
+    np.testing.assert_allclose(f, ref, rtol=1e-12)
+    assert np.all(cnt[:, 0] == 50)  # theta=0 never merges: one ray per source
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.6])
+def test_full_refinement_is_cell_by_cell(oracle_lib, theta):
+    P = workloads.uniform_box(n_gas=3000, n_src=40, seed=8)
+    rng = np.random.default_rng(1)
+    P["alpha"] = workloads.lognormal_alpha(rng, P["gas_xyz"], 1.0, 1.5, 0.1, n_modes=64)
+    T = _tree(oracle_lib, P)
+    lo, hi, abar = _leaf_boxes(T)
+    for sink in (0, 17, 999, 2998):
+        I = T.interactions(sink, theta, 0.0)
+        assert len(I["tau"]) > 0
+        p = P["gas_xyz"][:, sink].astype(np.float64)
+        for k in range(len(I["tau"])):
+            q = I["q"][k]
+            ell = _clip_all(lo, hi, p, q)
+            tau_bf = float(np.sum(abar * ell))
+            assert abs(I["tau"][k] - tau_bf) <= 1e-9 * max(1.0, tau_bf)
+            # at full refinement the segments are the leaves the ray crosses (up to
+            # boxes grazed at a face or an edge, which the fp32 test may drop)
+            assert abs(I["nseg"][k] - np.count_nonzero(ell > 0)) <= 2
+
+
+@pytest.mark.parametrize("tau_ref", [0.0, 0.05, 1e6])
+def test_segments_tile_the_ray(oracle_lib, tau_ref):
+    P = workloads.uniform_box(n_gas=4000, n_src=30, seed=12)
+    rng = np.random.default_rng(2)
+    P["alpha"] = workloads.lognormal_alpha(rng, P["gas_xyz"], 1.0, 1.0, 0.1, n_modes=64)
+    T = _tree(oracle_lib, P)
+    for sink in (5, 1234, 3999):
+        I = T.interactions(sink, 0.75, tau_ref)
+        p = P["gas_xyz"][:, sink].astype(np.float64)
+        s = np.linalg.norm(I["q"] - p[None, :], axis=1)
+        np.testing.assert_allclose(I["len_sum"], s, rtol=1e-12, atol=1e-15)
+
+
+def test_no_refinement_segment_bound(oracle_lib):
+    # tau_ref = 1e6 never refines: the segments are S, C and the siblings along
+    # the two paths to the common ancestor, so at most depth(S)+depth(C) of them
+    P = workloads.uniform_box(n_gas=4096, n_src=64, seed=0)
+    rng = np.random.default_rng(3)
+    P["alpha"] = workloads.lognormal_alpha(rng, P["gas_xyz"], 1.0, 2.0, 0.05, n_modes=64)
+    T = _tree(oracle_lib, P)
+    N = T.nodes()
+    leaf_of = T.particles()["leaf_of"]
+    rank = np.argsort(T.particles()["perm"])
+    for sink in (3, 333, 3333):
+        I = T.interactions(sink, 0.75, 1e6)
+        S = leaf_of[rank[sink]]
+        for k in range(len(I["node"])):
+            assert I["nseg"][k] <= N["depth"][S] + N["depth"][I["node"][k]]
+        _, cnt, _ = T.flux(0.75, 1e6, sinks=np.array([sink]), with_counters=True)
+        assert cnt[0, 3] == 0  # no refinement
+
+
+@pytest.mark.parametrize("theta,tau_ref", [(0.3, 0.01), (0.75, 0.1), (1.0, 0.5)])
+def test_uniform_medium_closed_form(oracle_lib, theta, tau_ref):
+    # Stromgren-like: one source of L=1 at the centre, alpha=20 (tau=10 centre->face)
+    P = workloads.stromgren(n_gas=4096, seed=1, theta=theta, tau_ref=tau_ref)
+    T = _tree(oracle_lib, P)
+    f, cnt, _ = T.flux(theta, tau_ref, with_counters=True)
+    p = P["gas_xyz"].astype(np.float64)
+    r = np.linalg.norm(p - 0.5, axis=0)
+    ref = np.exp(-20.0 * r) / (4 * np.pi * r * r)
+    np.testing.assert_allclose(f, ref, rtol=1e-12)
+    assert np.all(cnt[:, 0] == 1) and np.all(cnt[:, 3] == 0)
+
+
+def test_walk_partitions_the_sources(oracle_lib):
+    P = workloads.uniform_box(n_gas=3000, n_src=500, seed=6)
+    T = _tree(oracle_lib, P)
+    N = T.nodes()
+    S = T.sources()
+    theta = 0.7
+    h = 1.0 / G
+    for sink in (0, 1500, 2999):
+        I = T.interactions(sink, theta, 0.1)
+        p = P["gas_xyz"][:, sink].astype(np.float64)
+        covered = np.zeros(T.n_src, np.int64)
+        for k in range(len(I["node"])):
+            X = I["node"][k]
+            if I["src"][k] >= 0:
+                covered[I["src"][k]] += 1
+                assert N["split_bit"][X] < 0
+            else:
+                a, c = N["src_first"][X], N["src_count"][X]
+                covered[a:a + c] += 1
+                # accepted: l < theta * r (Eq. openangle), up to fp32 rounding
+                lo = N["glo"][X] * h
+                hi = N["ghi"][X] * h
+                r = np.linalg.norm(np.maximum(np.maximum(lo - p, p - hi), 0))
+                assert N["lrad"][X] < theta * r * (1 + 1e-6)
+                np.testing.assert_allclose(I["q"][k], N["cen"][X], rtol=0, atol=0)
+            par = N["parent"][X]
+            if par >= 0:  # the parent was opened
+                lo = N["glo"][par] * h
+                hi = N["ghi"][par] * h
+                r = np.linalg.norm(np.maximum(np.maximum(lo - p, p - hi), 0))
+                assert N["lrad"][par] >= theta * r * (1 - 1e-6)
+        assert np.all(covered == 1)
+
+
+def test_shadow_behind_occluder(oracle_lib):
+    rng = np.random.default_rng(30)
+    n = 20000
+    gas = rng.random((3, n)).astype(np.float32)
+    alpha = np.ones(n, np.float32)
+    inside = np.all((gas >= 0.45) & (gas <= 0.55), axis=0)
+    alpha[inside] *= 1e3
+    src = np.array([[0.2], [0.5], [0.5]], np.float32)
+    lum = np.ones(1, np.float32)
+    T = oracle_lib.OracleTree(gas, alpha, src, lum, bucket=8)
+    T0 = oracle_lib.OracleTree(gas, np.ones(n, np.float32), src, lum, bucket=8)
+    behind = np.nonzero((gas[0] > 0.65) & (gas[0] < 0.9) & (np.abs(gas[1] - 0.5) < 0.02)
+                        & (np.abs(gas[2] - 0.5) < 0.02))[0]
+    assert len(behind) > 5
+    f = T.flux(0.75, 0.1, sinks=behind)
+    f0 = T0.flux(0.75, 0.1, sinks=behind)
+    assert np.all(f <= np.exp(-30.0) * f0)  # tau through the core of the cube ~ 100
+    side = np.nonzero((gas[0] < 0.3) & (np.abs(gas[1] - 0.5) < 0.1))[0]
+    fs = T.flux(0.75, 0.1, sinks=side)
+    fs0 = T0.flux(0.75, 0.1, sinks=side)
+    np.testing.assert_allclose(fs, fs0, rtol=0.05)  # no shadow on the source's side
+
+
+def test_refinement_error_below_tau_ref(oracle_lib):
+    # Sec. 3.1.3 / Eq. reffrac: RMS error vs a fully refined reference lies below tau_ref
+    P = workloads.uniform_box(n_gas=6000, n_src=200, seed=13)
+    rng = np.random.default_rng(14)
+    P["alpha"] = workloads.lognormal_alpha(rng, P["gas_xyz"], 1.0, 2.0, 0.05, n_modes=128)
+    T = _tree(oracle_lib, P)
+    sinks = np.arange(0, 6000, 10)
+    ref = T.flux(0.75, 1e-8, sinks=sinks)
+    prev = None
+    for tau_ref in (1.0, 0.3, 0.1, 0.03):
+        f, cnt, _ = T.flux(0.75, tau_ref, sinks=sinks, with_counters=True)
+        rms = np.sqrt(np.mean(((f - ref) / ref) ** 2))
+        assert rms <= tau_ref
+        if prev is not None:
+            assert cnt[:, 1].sum() >= prev  # tighter tau_ref, more segments
+        prev = cnt[:, 1].sum()
+
+
+def test_theta_error_grows_with_theta(oracle_lib):
+    P = workloads.uniform_box(n_gas=4096, n_src=1024, seed=0)
+    T = _tree(oracle_lib, P)
+    sinks = np.arange(0, 4096, 8)
+    f0 = T.flux(0.0, 0.1, sinks=sinks)
+    errs, rays = [], []
+    for theta in (0.3, 0.6, 0.9):
+        f, cnt, _ = T.flux(theta, 0.1, sinks=sinks, with_counters=True)
+        errs.append(np.sqrt(np.mean(((f - f0) / f0) ** 2)))
+        rays.append(cnt[:, 0].mean())
+    assert errs[0] < errs[1] < errs[2] < 0.05
+    assert rays[0] > rays[1] > rays[2]
+
+
+def test_weights_and_subsets(oracle_lib):
+    P = workloads.uniform_box(n_gas=2000, n_src=20, seed=15)
+    rng = np.random.default_rng(16)
+    P["weight"] = rng.uniform(0.2, 3.0, 2000).astype(np.float32)
+    T = _tree(oracle_lib, P)
+    full = T.flux(0.75, 0.1)
+    sub = np.array([1999, 3, 500, 3])
+    np.testing.assert_array_equal(T.flux(0.75, 0.1, sinks=sub), full[sub])
+    with pytest.raises(oracle_lib.OracleError):
+        T.flux(0.75, 0.1, sinks=np.array([2000]))
