@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark of the TREVR hot path on GB300: sink fluxes per second.
+
+One step = build the radiation tree from the particles (keys, sort, topology,
+source deposit, cell moments) + the flux at every sink (source walk, reverse
+rays with tau_ref refinement, flux sum), on inputs already resident in HBM.
+
+Prints one JSON line (rank 0). See the design doc for the workloads, the roofline
+arithmetic and the CPU baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload clumpy|stromgren|uniform]
+    python bench.py --impl reference ...   # the FP64 CPU oracle as the reference arm
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "sink fluxes/s"
+UNIT = "fluxes/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def _problem(name, seed_offset=0):
+    if name == "clumpy":
+        P = workloads.clumpy(seed=2 + seed_offset)
+        desc = "clumpy lognormal medium (sigma_ln=2, corr 0.05) + x1e3 cube occluder"
+    elif name == "stromgren":
+        P = workloads.stromgren(seed=1 + seed_offset)
+        desc = "Stromgren-like: one L=1 source at the centre, uniform alpha=20"
+    elif name == "uniform":
+        P = workloads.uniform_box(seed=0 + seed_offset)
+        desc = "uniform box, 4096 gas / 64 sources, alpha=1"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return P, desc
+
+
+def _config(P, name, desc):
+    return {"workload": f"{name}: {desc}", "n_gas": int(P["gas_xyz"].shape[1]),
+            "n_src": int(P["src_xyz"].shape[1]), "theta_open": P["theta"],
+            "tau_ref": P["tau_ref"], "bucket": P["bucket"], "seed": P["seed"],
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _oracle_baseline(P, n_gas, sample_n, seed=7):
+    """Time the FP64 oracle as it stands on the host cores on a bounded sample:
+    the full tree build plus the flux at `sample_n` sinks. Returns (value, info, sinks,
+    flux)."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    T = oracle.OracleTree(P["gas_xyz"], P["alpha"], P["src_xyz"], P["src_lum"], lo=P["lo"],
+                          side=P["side"], bucket=P["bucket"])
+    t_build = time.perf_counter() - t0
+    sinks = workloads.sink_sample(n_gas, sample_n, seed=seed)
+    t0 = time.perf_counter()
+    f = T.flux(P["theta"], P["tau_ref"], sinks=sinks, nthreads=cores)
+    t_walk = time.perf_counter() - t0
+    # build time is charged in proportion to the sample's share of the sinks
+    per_sink = t_walk / len(sinks) + t_build / n_gas
+    info = {"value": 1.0 / per_sink, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(sinks)} of {n_gas} sinks walked (seeded) + the full {n_gas}-particle "
+                      f"tree build charged pro rata; walk {t_walk:.2f} s, build {t_build:.2f} s",
+            "walk_s": t_walk, "build_s": t_build}
+    return info, sinks, f, T
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if world > 1 and rank != 0:
+        return
+    P, desc = _problem(args.workload)
+    n = int(P["gas_xyz"].shape[1])
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    T = oracle.OracleTree(P["gas_xyz"], P["alpha"], P["src_xyz"], P["src_lum"], lo=P["lo"],
+                          side=P["side"], bucket=P["bucket"])
+    t_build = time.perf_counter() - t0
+    sample_n = min(n, args.ref_sample)
+    times = []
+    for step in range(args.warmup + args.steps):
+        sinks = workloads.sink_sample(n, sample_n, seed=100 + step)
+        t0 = time.perf_counter()
+        T.flux(P["theta"], P["tau_ref"], sinks=sinks, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt + t_build * sample_n / n)
+    per_step = sum(times) / len(times)
+    value = sample_n / per_step
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(P, args.workload, desc),
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT,
+                             "sample": f"each step walks {sample_n} seeded sinks of {n}; the "
+                                       f"{n}-particle tree build ({t_build:.2f} s, once) is "
+                                       f"charged pro rata"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    from paper_1902_08083_gb300 import trevr
+
+    rank, world, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    # weak scaling: every rank solves its own instance of the workload (seed + rank)
+    P, desc = _problem(args.workload, seed_offset=rank)
+    n = int(P["gas_xyz"].shape[1])
+    stream = torch.cuda.current_stream()
+    g = {k: torch.from_numpy(np.ascontiguousarray(P[k])).to(dev)
+         for k in ("gas_xyz", "alpha", "src_xyz", "src_lum")}
+    flux = torch.empty(n, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(timed_events=None):
+        tree = trevr.build_tree(g["gas_xyz"], g["alpha"], g["src_xyz"], g["src_lum"],
+                                lo=P["lo"], side=P["side"], bucket=P["bucket"], stream=stream)
+        if timed_events is not None:
+            timed_events[1].record(stream)
+        trevr.compute_flux(tree, P["theta"], P["tau_ref"], out=flux, stream=stream)
+        if timed_events is not None:
+            timed_events[2].record(stream)
+        return tree
+
+    # counters (untimed) for the algorithmic-bytes figure
+    tree = step()
+    _, st = trevr.compute_flux(tree, P["theta"], P["tau_ref"], out=flux, stats=True,
+                               stream=stream)
+    tree.free()
+    for _ in range(args.warmup):
+        step().free()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = trevr.kernel_launches()
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush outside the timed interval
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        t = step(e)
+        evs.append(e)
+        t.free()
+    torch.cuda.synchronize()
+    launches = trevr.kernel_launches() - launches0
+    clk = clocks.stop()
+    step_ms = [e[0].elapsed_time(e[2]) for e in evs]
+    build_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    walk_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    t_step = sum(step_ms) / len(step_ms)
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(tt.item())
+        torch.distributed.barrier()
+    value = world * n / (t_step * 1e-3)
+
+    # end to end through the public API with host buffers: pinned H2D of the
+    # step's inputs, build, flux, D2H of the fluxes, all inside the timed region
+    host = {k: torch.from_numpy(np.ascontiguousarray(P[k])).pin_memory()
+            for k in ("gas_xyz", "alpha", "src_xyz", "src_lum")}
+    hflux = torch.empty(n, dtype=torch.float32).pin_memory()
+    dbuf = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = hflux.numel() * 4
+
+    def e2e_step():
+        for k in host:
+            dbuf[k].copy_(host[k], non_blocking=True)
+        tr = trevr.build_tree(dbuf["gas_xyz"], dbuf["alpha"], dbuf["src_xyz"], dbuf["src_lum"],
+                              lo=P["lo"], side=P["side"], bucket=P["bucket"], stream=stream)
+        trevr.compute_flux(tr, P["theta"], P["tau_ref"], out=flux, stream=stream)
+        hflux.copy_(flux, non_blocking=True)
+        stream.synchronize()
+        tr.free()
+
+    e2e_step()
+    e2e_ms = []
+    for _ in range(max(2, min(args.steps, 5))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    t_e2e = sum(e2e_ms) / len(e2e_ms)
+    if world > 1:
+        tt = torch.tensor([t_e2e], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (the sink walk): algorithmic bytes per launch =
+    # 20 B per sink (position, leaf, flux) + 32 B per source cell tested + 32 B per
+    # cell clipped by a ray, divided by the walk's event-timed duration
+    alg_bytes = 20 * n + 32 * st["src_nodes_visited"] + 32 * st["cells_clipped"]
+    t_walk = sum(walk_ms) / len(walk_ms) * 1e-3
+    peak, peak_kind = _peaks()
+    achieved = alg_bytes / t_walk / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "walk_plain_kernel",
+                "peak_kind": f"{peak_kind} (copy bandwidth, burst)",
+                "bytes_per_launch": alg_bytes}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": _config(P, args.workload, desc),
+            "build_ms": sum(build_ms) / len(build_ms), "walk_ms": t_walk * 1e3,
+            "walk_only_fluxes_per_s": world * n / t_walk,
+            "interactions_per_s": world * st["interactions"] / t_walk,
+            "per_sink": {"interactions": st["interactions"] / n, "segments": st["segments"] / n,
+                         "cells_visited": st["src_nodes_visited"] / n,
+                         "refinements": st["refine_expansions"] / n,
+                         "cells_clipped": st["cells_clipped"] / n},
+            "roofline": roofline,
+            "e2e": {"value": world * n / (t_e2e * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches), "clocks": clk}
+
+    if world == 1 and not args.no_cpu_baseline:
+        info, sinks, fo, _ = _oracle_baseline(P, n, args.cpu_sample)
+        fg = flux.cpu().numpy()[sinks].astype(np.float64)
+        big = fo >= 1e-30
+        rel = np.abs(fg[big] - fo[big]) / fo[big]
+        line["cpu_baseline"] = {k: info[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["parity"] = {"sinks": int(len(sinks)), "median_rel_err": float(np.median(rel)),
+                          "max_rel_err": float(rel.max()),
+                          "pass": bool(np.median(rel) <= 1e-5 and rel.max() <= 1e-3)}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="clumpy", choices=["clumpy", "stromgren", "uniform"])
+    ap.add_argument("--cpu-sample", type=int, default=2048)
+    ap.add_argument("--ref-sample", type=int, default=512)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

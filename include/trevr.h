@@ -1,0 +1,174 @@
+/*
+ * trevr.h -- C ABI of the GB300 (sm_103a) implementation of the TREVR hot path.
+ *
+ * TREVR (Grond, Woods, Wadsley & Couchman 2019, arXiv:1902.08083) computes,
+ * for every sink (gas particle), the angle-averaged intensity
+ *
+ *     F_p = sum over pseudo-sources C of  L_C exp(-tau_pC) / (4 pi s_pC^2)   (Eq. simpint)
+ *
+ * where the pseudo-sources come from a walk of a space-filling source tree
+ * under the opening-angle criterion theta_open > l/r (Eq. openangle, Sec.
+ * 2.2.1) and tau_pC is the optical depth of the reverse ray from the sink to
+ * the pseudo-source, summed over tree cells (Eqs. taui, tausum, Sec. 2.2.2) and
+ * refined into child cells where tau_ref < tau_max - tau_min (Eq. refcrit,
+ * Sec. 2.2.3).
+ *
+ * Conventions for every entry point:
+ *   - Array arguments are DEVICE pointers on the current CUDA device unless
+ *     marked "host". The caller owns them; the library never frees them and
+ *     never keeps them past the call (the tree copies what it needs).
+ *   - Positions are structure-of-arrays: xyz points to 3*n floats laid out as
+ *     x[0..n), y[0..n), z[0..n).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream). Work is enqueued on it; see each function for when it syncs.
+ *   - The return value is TREVR_OK (0) or one of the TREVR_ERR_* codes below.
+ *     Errors found on the device (a point outside the domain, a non-finite
+ *     input, a traversal stack overflow) are reported through a device status
+ *     word read back at the function's sync point; the kernels never trap.
+ *     Outputs are undefined when the return value is not TREVR_OK.
+ *   - Particle and source counts are limited to 2^30 (indices are 32-bit).
+ */
+#ifndef TREVR_H
+#define TREVR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TREVR_OK 0
+#define TREVR_ERR_INVALID_ARGUMENT 1 /* null pointer, bad size or parameter, NaN/negative input */
+#define TREVR_ERR_OUT_OF_DOMAIN 2    /* a particle or source outside [lo, lo+side)^3 */
+#define TREVR_ERR_STACK_OVERFLOW 3   /* a traversal stack would overflow (stack_depth too small) */
+#define TREVR_ERR_ITERATION_LIMIT 4  /* a walk exceeded its iteration cap (hang guard) */
+#define TREVR_ERR_CUDA 5             /* a CUDA runtime call failed */
+#define TREVR_ERR_OUT_OF_MEMORY 6    /* device allocation failed */
+
+typedef struct trevr_tree trevr_tree; /* opaque, device-resident, owned by the library */
+
+/* Cubic domain: every particle and source must satisfy lo_d <= x_d < lo_d + side,
+   evaluated in fp32. */
+typedef struct {
+    float lo[3];
+    float side;
+} trevr_domain;
+
+/* The method's parameters (Sec. 2.2): theta_open (Eq. openangle, >= 0),
+   tau_ref (Eq. refcrit; <= 0 means refine every cell down to the buckets) and
+   the bucket size N_B (>= 1). The three tuning fields pick the launch shape of
+   the sink walk; 0 selects the library default. */
+typedef struct {
+    float theta_open;
+    float tau_ref;
+    int bucket;
+    int sinks_per_warp; /* 0 = default */
+    int block_size;     /* threads per block of the walk, 0 = default */
+    int stack_depth;    /* traversal stack entries per sink, 0 = default (64) */
+} trevr_params;
+
+/* Totals over the sinks of one call, and timings (ms, CUDA events). */
+typedef struct {
+    long long interactions;      /* rays traced: accepted cells plus single sources */
+    long long segments;          /* ray segments summed (cells whose mean absorption was used) */
+    long long src_nodes_visited; /* source-tree cells tested against the opening angle */
+    long long refine_expansions; /* cells replaced by their two children (Eq. refcrit) */
+    long long cells_clipped;     /* ray/cell intersection tests (every cell record a ray read) */
+    float build_ms;
+    float walk_ms;
+} trevr_stats;
+
+/*
+ * Build the radiation tree (Sec. 2.2, 2.3): Morton keys of the gas particles
+ * (21 bits per axis, x most significant), a stable radix sort, the binary tree
+ * of Morton prefixes with leaves of at most N_B particles (or of equal keys),
+ * cut by planes so that the cells fill the domain; the sources deposited into
+ * the leaves that hold them; and the cell moments: volume-weighted mean
+ * absorption sum(w alpha)/sum(w) (Sec. 2.3, with w = m/rho this is
+ * rho_cell = sum m / sum(m/rho) times kappa), the directional alpha_min /
+ * alpha_max built bottom-up (Sec. 2.2.3), total luminosity and centre of
+ * luminosity (Sec. 2.2.1).
+ *
+ *   gas_xyz  3*n_gas floats (SoA), gas particle positions; the sinks.
+ *   alpha    n_gas floats, absorption coefficient alpha = kappa*rho >= 0.
+ *   weight   n_gas floats > 0 (volume weight m/rho), or NULL for all 1.
+ *   n_gas    1 .. 2^30.
+ *   src_xyz  3*n_src floats (SoA), source positions.
+ *   src_lum  n_src floats, luminosities >= 0.
+ *   n_src    0 .. 2^30.
+ *   dom      host pointer to the domain.
+ *   prm      host pointer; only prm->bucket is used here.
+ *   stream   cudaStream_t.
+ *   out      host pointer; receives the tree (free with trevr_tree_free).
+ * Synchronises `stream` before returning (the status word is read back).
+ */
+int trevr_build_tree(const float* gas_xyz, const float* alpha, const float* weight,
+                     long long n_gas, const float* src_xyz, const float* src_lum, long long n_src,
+                     const trevr_domain* dom, const trevr_params* prm, void* stream,
+                     trevr_tree** out);
+
+/*
+ * Flux at the sinks (Eq. simpint summed over the pseudo-sources of the
+ * opening-angle walk, Sec. 2.2.1-2.2.3), in fp32 with the optical depth
+ * accumulated by compensated summation.
+ *
+ *   t         tree from trevr_build_tree.
+ *   sink_idx  n_sink int64 caller indices of gas particles, or NULL = all
+ *             gas particles in the caller's order (then n_sink must be n_gas).
+ *   prm       host pointer: theta_open, tau_ref, tuning fields.
+ *   flux_out  n_sink floats: flux_out[k] is the flux at sink k.
+ *   sink_counters  NULL, or 4*n_sink int32: per sink the number of rays,
+ *             segments, source cells visited and refinements.
+ *   stats     host pointer or NULL. When non-NULL the call synchronises the
+ *             stream and fills the totals and walk time; when NULL the call
+ *             is asynchronous and device errors surface at the next call
+ *             that synchronises (trevr_check).
+ */
+int trevr_compute_flux(const trevr_tree* t, const long long* sink_idx, long long n_sink,
+                       const trevr_params* prm, float* flux_out, int* sink_counters,
+                       trevr_stats* stats, void* stream);
+
+/* Synchronise `stream` and return the first device error recorded on the tree
+   since the last check (TREVR_OK if none), clearing it. */
+int trevr_check(const trevr_tree* t, void* stream);
+
+/* Number of cells of the tree, the maximum cell depth, and the particle and
+   source counts (host pointers, any may be NULL). */
+int trevr_tree_info(const trevr_tree* t, long long* n_nodes, int* max_depth, long long* n_gas,
+                    long long* n_src);
+
+/*
+ * Copy the tree out (for tests and tools). Node arrays are indexed by the
+ * library's breadth-first cell numbering (root = 1, the children of a cell
+ * are two consecutive cells 2k, 2k+1; entry 0 is unused), n_nodes+1 entries;
+ * any pointer may be NULL. All are device pointers.
+ *   key      n_gas uint64 Morton keys in sorted order;  perm n_gas int32 caller
+ *            index of the i-th sorted particle;  leaf_of n_gas int32 leaf cell of
+ *            the i-th sorted particle.
+ *   first, count   int32 particle range of each cell in sorted order.
+ *   child    int32 lower child (upper = child+1), -1 for a leaf.
+ *   parent   int32 (0 for the root).   depth int32.
+ *   glo, ghi 3 int32 per cell: integer box on the 2^21 grid, [glo, ghi).
+ *   abar     fp32 mean absorption;  dalpha fp32 alpha_max - alpha_min;
+ *   lum      fp32 total luminosity;  cen 3 fp32 centre of luminosity;
+ *   l2       fp32 squared distance from the centre to the furthest vertex.
+ *   src_first, src_count  int32 range of each cell in the sorted sources;
+ *   src_order n_src int32 caller index of the k-th sorted source.
+ */
+int trevr_tree_export(const trevr_tree* t, unsigned long long* key, int* perm, int* leaf_of,
+                      int* first, int* count, int* child, int* parent, int* depth, int* glo,
+                      int* ghi, float* abar, float* dalpha, float* lum, float* cen, float* l2,
+                      int* src_first, int* src_count, int* src_order, void* stream);
+
+/* Release the tree and every buffer it holds (synchronises the device). */
+void trevr_tree_free(trevr_tree* t);
+
+/* Number of CUDA kernels this library has launched in the calling process
+   (all devices, all streams); for launch accounting in benchmarks. */
+unsigned long long trevr_kernel_launches(void);
+
+/* Short English description of a status code (static storage). */
+const char* trevr_status_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TREVR_H */

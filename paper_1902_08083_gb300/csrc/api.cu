@@ -1,0 +1,275 @@
+// C ABI of libtrevr: argument checks, status mapping, dispatch to the kernels.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstring>
+
+#include "trevr.h"
+#include "trevr_internal.cuh"
+
+namespace trevr {
+
+int status_to_error(int bits) {
+  if (bits & kStatusInvalid) return TREVR_ERR_INVALID_ARGUMENT;
+  if (bits & kStatusOutOfDomain) return TREVR_ERR_OUT_OF_DOMAIN;
+  if (bits & kStatusStackOverflow) return TREVR_ERR_STACK_OVERFLOW;
+  if (bits & kStatusIterationLimit) return TREVR_ERR_ITERATION_LIMIT;
+  return TREVR_OK;
+}
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+int cuda_to_error(cudaError_t e) {
+  if (e == cudaSuccess) return TREVR_OK;
+  if (e == cudaErrorMemoryAllocation) return TREVR_ERR_OUT_OF_MEMORY;
+  return TREVR_ERR_CUDA;
+}
+
+static WalkParams walk_params(const trevr_tree* t, const trevr_params* prm) {
+  WalkParams wp;
+  volatile float th = prm->theta_open;
+  wp.theta2 = th * th;
+  wp.tau_ref = prm->tau_ref;
+  volatile float smin = 1e-12f * t->side;
+  wp.smin2 = smin * smin;
+  wp.stack_depth = prm->stack_depth > 0 ? prm->stack_depth : kDefaultStack;
+  return wp;
+}
+
+static bool params_ok(const trevr_params* prm) {
+  if (!prm) return false;
+  if (!(prm->theta_open >= 0.0f) || !std::isfinite(prm->theta_open)) return false;
+  if (std::isnan(prm->tau_ref)) return false;
+  if (prm->stack_depth < 0 || prm->stack_depth > kMaxStack) return false;
+  if (prm->block_size < 0 || prm->block_size > 1024 || (prm->block_size % 32) != 0) return false;
+  if (prm->sinks_per_warp < 0) return false;
+  return true;
+}
+
+}  // namespace trevr
+
+using namespace trevr;
+
+TreeView trevr_tree::view() const {
+  TreeView v;
+  v.n_gas = (int)n_gas;
+  v.n_src = (int)n_src;
+  v.n_nodes_cap = (int)(n_nodes + 1);
+  v.bucket = bucket;
+  for (int d = 0; d < 3; ++d) v.lo[d] = lo[d];
+  v.side = side;
+  v.h = h;
+  v.key = key;
+  v.perm = perm;
+  v.rank = rank;
+  v.leaf_of = leaf_of;
+  v.pos = pos;
+  v.w = w;
+  v.nA = nA;
+  v.nB = nB;
+  v.nS = nS;
+  v.nT = nT;
+  v.nl2 = nl2;
+  v.ndepth = ndepth;
+  v.nfirst = nfirst;
+  v.ncount = ncount;
+  v.src = src;
+  v.src_order = src_order;
+  v.n_nodes = d_n_nodes;
+  return v;
+}
+
+extern "C" {
+
+int trevr_build_tree(const float* gas_xyz, const float* alpha, const float* weight,
+                     long long n_gas, const float* src_xyz, const float* src_lum, long long n_src,
+                     const trevr_domain* dom, const trevr_params* prm, void* stream,
+                     trevr_tree** out) {
+  if (!out) return TREVR_ERR_INVALID_ARGUMENT;
+  *out = nullptr;
+  if (!gas_xyz || !alpha || !dom || !prm) return TREVR_ERR_INVALID_ARGUMENT;
+  if (n_gas < 1 || n_gas > (1ll << 30) || n_src < 0 || n_src > (1ll << 30))
+    return TREVR_ERR_INVALID_ARGUMENT;
+  if (n_src > 0 && (!src_xyz || !src_lum)) return TREVR_ERR_INVALID_ARGUMENT;
+  if (prm->bucket < 1) return TREVR_ERR_INVALID_ARGUMENT;
+  if (!(dom->side > 0.0f) || !std::isfinite(dom->side)) return TREVR_ERR_INVALID_ARGUMENT;
+  for (int d = 0; d < 3; ++d)
+    if (!std::isfinite(dom->lo[d]) || !std::isfinite(dom->lo[d] + dom->side))
+      return TREVR_ERR_INVALID_ARGUMENT;
+  float ms = 0.0f;
+  return build_tree_impl(gas_xyz, alpha, weight, n_gas, src_xyz, src_lum, n_src, dom,
+                         prm->bucket, (cudaStream_t)stream, out, &ms);
+}
+
+int trevr_compute_flux(const trevr_tree* t, const long long* sink_idx, long long n_sink,
+                       const trevr_params* prm, float* flux_out, int* sink_counters,
+                       trevr_stats* stats, void* stream) {
+  if (!t || !params_ok(prm)) return TREVR_ERR_INVALID_ARGUMENT;
+  if (n_sink < 0 || n_sink > (1ll << 30)) return TREVR_ERR_INVALID_ARGUMENT;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (n_sink == 0) return TREVR_OK;
+  if (!flux_out) return TREVR_ERR_INVALID_ARGUMENT;
+  if (!sink_idx && n_sink != t->n_gas) return TREVR_ERR_INVALID_ARGUMENT;
+  cudaStream_t s = (cudaStream_t)stream;
+  WalkParams wp = walk_params(t, prm);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (stats) {
+    cudaMemsetAsync(t->d_stats, 0, 5 * sizeof(unsigned long long), s);
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+  }
+  cudaError_t err = launch_walk(t->view(), sink_idx, (int)n_sink, wp, flux_out, sink_counters,
+                                stats ? t->d_stats : nullptr, t->status, prm->block_size, s);
+  if (err != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return cuda_to_error(err);
+  }
+  if (!stats) return TREVR_OK;
+  cudaEventRecord(e1, s);
+  unsigned long long h[5];
+  int status = 0;
+  cudaMemcpyAsync(h, t->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&status, t->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  err = cudaStreamSynchronize(s);
+  float ms = 0.0f;
+  if (err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return cuda_to_error(err);
+  stats->interactions = (long long)h[0];
+  stats->segments = (long long)h[1];
+  stats->src_nodes_visited = (long long)h[2];
+  stats->refine_expansions = (long long)h[3];
+  stats->cells_clipped = (long long)h[4];
+  stats->walk_ms = ms;
+  if (status) {
+    cudaMemsetAsync(t->status, 0, sizeof(int), s);
+    cudaStreamSynchronize(s);
+    return status_to_error(status);
+  }
+  return TREVR_OK;
+}
+
+int trevr_check(const trevr_tree* t, void* stream) {
+  if (!t) return TREVR_ERR_INVALID_ARGUMENT;
+  cudaStream_t s = (cudaStream_t)stream;
+  int status = 0;
+  cudaMemcpyAsync(&status, t->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaError_t err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) return cuda_to_error(err);
+  if (status) {
+    cudaMemsetAsync(t->status, 0, sizeof(int), s);
+    cudaStreamSynchronize(s);
+  }
+  return status_to_error(status);
+}
+
+int trevr_tree_info(const trevr_tree* t, long long* n_nodes, int* max_depth, long long* n_gas,
+                    long long* n_src) {
+  if (!t) return TREVR_ERR_INVALID_ARGUMENT;
+  if (n_nodes) *n_nodes = t->n_nodes;
+  if (max_depth) *max_depth = t->max_depth;
+  if (n_gas) *n_gas = t->n_gas;
+  if (n_src) *n_src = t->n_src;
+  return TREVR_OK;
+}
+
+namespace {
+__global__ void export_kernel(int ncell, const int4* nglo, const int4* nghi, const int4* nT,
+                              const float4* nA, const float4* nB, const float4* nS, int* child,
+                              int* parent, int* glo, int* ghi, float* abar, float* dalpha,
+                              float* lum, float* cen, int* src_first, int* src_count) {
+  int X = blockIdx.x * blockDim.x + threadIdx.x;
+  if (X >= ncell) return;
+  int4 t = nT[X];
+  if (child) child[X] = t.x;
+  if (parent) parent[X] = t.y;
+  if (src_first) src_first[X] = t.z;
+  if (src_count) src_count[X] = t.w;
+  int4 a = nglo[X], b = nghi[X];
+  if (glo) {
+    glo[3 * X] = a.x;
+    glo[3 * X + 1] = a.y;
+    glo[3 * X + 2] = a.z;
+  }
+  if (ghi) {
+    ghi[3 * X] = b.x;
+    ghi[3 * X + 1] = b.y;
+    ghi[3 * X + 2] = b.z;
+  }
+  float4 A = nA[X], B = nB[X], S = nS[X];
+  if (abar) abar[X] = A.w;
+  if (dalpha) dalpha[X] = B.w;
+  if (lum) lum[X] = S.w;
+  if (cen) {
+    cen[3 * X] = S.x;
+    cen[3 * X + 1] = S.y;
+    cen[3 * X + 2] = S.z;
+  }
+}
+}  // namespace
+
+int trevr_tree_export(const trevr_tree* t, unsigned long long* key, int* perm, int* leaf_of,
+                      int* first, int* count, int* child, int* parent, int* depth, int* glo,
+                      int* ghi, float* abar, float* dalpha, float* lum, float* cen, float* l2,
+                      int* src_first, int* src_count, int* src_order, void* stream) {
+  if (!t) return TREVR_ERR_INVALID_ARGUMENT;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)t->n_gas, nc = (size_t)t->n_nodes + 1;
+  if (key) cudaMemcpyAsync(key, t->key, n * sizeof(*key), cudaMemcpyDeviceToDevice, s);
+  if (perm) cudaMemcpyAsync(perm, t->perm, n * sizeof(int), cudaMemcpyDeviceToDevice, s);
+  if (leaf_of) cudaMemcpyAsync(leaf_of, t->leaf_of, n * sizeof(int), cudaMemcpyDeviceToDevice, s);
+  if (first) cudaMemcpyAsync(first, t->nfirst, nc * sizeof(int), cudaMemcpyDeviceToDevice, s);
+  if (count) cudaMemcpyAsync(count, t->ncount, nc * sizeof(int), cudaMemcpyDeviceToDevice, s);
+  if (depth) cudaMemcpyAsync(depth, t->ndepth, nc * sizeof(int), cudaMemcpyDeviceToDevice, s);
+  if (l2) cudaMemcpyAsync(l2, t->nl2, nc * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  if (src_order && t->n_src > 0)
+    cudaMemcpyAsync(src_order, t->src_order, (size_t)t->n_src * sizeof(int),
+                    cudaMemcpyDeviceToDevice, s);
+  export_kernel<<<(int)((nc + 255) / 256), 256, 0, s>>>(
+      (int)nc, t->nglo, t->nghi, t->nT, t->nA, t->nB, t->nS, child, parent, glo, ghi, abar, dalpha,
+      lum, cen, src_first, src_count);
+  note_launch();
+  cudaError_t err = cudaStreamSynchronize(s);
+  if (err == cudaSuccess) err = cudaGetLastError();
+  return cuda_to_error(err);
+}
+
+void trevr_tree_free(trevr_tree* t) {
+  if (!t) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(t->device);
+  cudaDeviceSynchronize();
+  void* ptrs[] = {t->key, t->perm,   t->rank,   t->leaf_of, t->pos,    t->w,      t->nA,
+                  t->nB,  t->nS,     t->nT,     t->nl2,     t->ndepth, t->nfirst, t->ncount,
+                  t->nglo, t->nghi,  t->src,    t->src_order, t->levels, t->d_n_nodes,
+                  t->status, t->d_stats};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  cudaSetDevice(cur);
+  delete t;
+}
+
+unsigned long long trevr_kernel_launches(void) {
+  return g_launches.load(std::memory_order_relaxed);
+}
+
+const char* trevr_status_string(int code) {
+  switch (code) {
+    case TREVR_OK: return "ok";
+    case TREVR_ERR_INVALID_ARGUMENT: return "invalid argument";
+    case TREVR_ERR_OUT_OF_DOMAIN: return "point outside the domain";
+    case TREVR_ERR_STACK_OVERFLOW: return "traversal stack overflow";
+    case TREVR_ERR_ITERATION_LIMIT: return "walk iteration limit reached";
+    case TREVR_ERR_CUDA: return "CUDA error";
+    case TREVR_ERR_OUT_OF_MEMORY: return "out of device memory";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

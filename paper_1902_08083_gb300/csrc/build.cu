@@ -1,0 +1,832 @@
+// Radiation-tree build on the GPU (Grond et al. 2019, Sec. 2.2 and 2.3):
+// Morton keys -> stable radix sort -> top-down binary tree of Morton prefixes,
+// level by level -> source deposit -> bottom-up cell moments, level by level.
+//
+// Every kernel is launched with a fixed grid and reads the extent of its level
+// from device memory, so the whole topology pass runs without host round trips;
+// the host synchronises once, after the topology, to size the moment pass.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstring>
+#include <vector>
+
+#include "primitives.cuh"
+#include "trevr_internal.cuh"
+
+namespace trevr {
+
+// ------------------------------------------------------------------------------------
+// Morton keys
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long expand3(unsigned v) {
+  unsigned long long x = v & 0x1fffffull;
+  x = (x | (x << 32)) & 0x1f00000000ffffull;
+  x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+  x = (x | (x << 8)) & 0x100f00f00f00f00full;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+
+__device__ __forceinline__ unsigned compact3(unsigned long long x) {
+  x &= 0x1249249249249249ull;
+  x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+  x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+  x = (x ^ (x >> 8)) & 0x1f0000ff0000ffull;
+  x = (x ^ (x >> 16)) & 0x1f00000000ffffull;
+  x = (x ^ (x >> 32)) & 0x1fffffull;
+  return (unsigned)x;
+}
+
+// grid coordinate of key along axis a (0 = x, the most significant)
+__device__ __forceinline__ unsigned key_coord(unsigned long long key, int a) {
+  return compact3(key >> (2 - a));
+}
+
+struct Domain32 {
+  float lo[3], hi[3], scale, h;
+};
+
+// q = floor((x - lo) * scale) in fp32 (one rounded subtraction, one rounded
+// multiplication), clamped to 2^21 - 1. Caller has checked lo <= x < hi.
+__device__ __forceinline__ unsigned quantize(float x, float lo, float scale) {
+  float t = __fmul_rn(__fsub_rn(x, lo), scale);
+  unsigned q = __float2uint_rz(t);
+  return q > (unsigned)(kGridMax - 1) ? (unsigned)(kGridMax - 1) : q;
+}
+
+__device__ __forceinline__ bool in_dom(float x, float lo, float hi) { return x >= lo && x < hi; }
+
+__global__ void keys_kernel(const float* __restrict__ xyz, const float* __restrict__ alpha,
+                            const float* __restrict__ weight, int n, Domain32 D,
+                            unsigned long long* __restrict__ keys, unsigned* __restrict__ vals,
+                            int* status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float x = xyz[i], y = xyz[(size_t)n + i], z = xyz[2 * (size_t)n + i];
+  int bad = 0;
+  unsigned long long k = 0;
+  if (in_dom(x, D.lo[0], D.hi[0]) && in_dom(y, D.lo[1], D.hi[1]) && in_dom(z, D.lo[2], D.hi[2])) {
+    k = (expand3(quantize(x, D.lo[0], D.scale)) << 2) |
+        (expand3(quantize(y, D.lo[1], D.scale)) << 1) | expand3(quantize(z, D.lo[2], D.scale));
+  } else {
+    bad |= kStatusOutOfDomain;
+  }
+  float a = alpha[i];
+  if (!(a >= 0.0f) || !isfinite(a)) bad |= kStatusInvalid;
+  if (weight) {
+    float wv = weight[i];
+    if (!(wv > 0.0f) || !isfinite(wv)) bad |= kStatusInvalid;
+  }
+  if (bad) atomicOr(status, bad);
+  keys[i] = k;
+  vals[i] = (unsigned)i;
+}
+
+// ------------------------------------------------------------------------------------
+// Device-wide exclusive scan (unsigned, in place)
+// ------------------------------------------------------------------------------------
+__global__ void scan_tile_kernel(unsigned* data, int n, unsigned* tile_sums) {
+  __shared__ unsigned smem[32];
+  const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  unsigned v[kScanItems];
+  unsigned s = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    v[j] = (base + j < n) ? data[base + j] : 0u;
+    s += v[j];
+  }
+  unsigned total;
+  unsigned off = block_exclusive_scan(s, smem, &total);
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    if (base + j < n) data[base + j] = off;
+    off += v[j];
+  }
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+__global__ void scan_add_kernel(unsigned* data, int n, const unsigned* tile_offsets) {
+  const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  const unsigned o = tile_offsets[blockIdx.x];
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j)
+    if (base + j < n) data[base + j] += o;
+}
+
+static int scan_tiles(int n) { return (n + kScanTile - 1) / kScanTile; }
+
+// scratch must hold scan_scratch_words(n) unsigned
+static size_t scan_scratch_words(int n) {
+  size_t w = 0;
+  while (n > 1) {
+    n = scan_tiles(n);
+    w += (size_t)n;
+  }
+  return w + 1;
+}
+
+static void exclusive_scan(unsigned* data, int n, unsigned* scratch, cudaStream_t s) {
+  if (n <= 0) return;
+  int tiles = scan_tiles(n);
+  scan_tile_kernel<<<tiles, kScanThreads, 0, s>>>(data, n, scratch);
+  note_launch();
+  if (tiles > 1) {
+    exclusive_scan(scratch, tiles, scratch + tiles, s);
+    scan_add_kernel<<<tiles, kScanThreads, 0, s>>>(data, n, scratch);
+    note_launch();
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Stable LSD radix sort, 8-bit digits. counts layout: [digit][tile].
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(
+    const unsigned long long* __restrict__ keys, int n, int shift, unsigned* __restrict__ counts,
+    int n_tiles) {
+  __shared__ unsigned hist[256];
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[d] = 0;
+  __syncthreads();
+  const int base = blockIdx.x * kSortTile;
+  for (int r = 0; r < kSortItems; ++r) {
+    int i = base + r * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&hist[(unsigned)(keys[i] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += blockDim.x)
+    counts[(size_t)d * n_tiles + blockIdx.x] = hist[d];
+}
+
+__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
+    const unsigned long long* __restrict__ kin, const unsigned* __restrict__ vin,
+    unsigned long long* __restrict__ kout, unsigned* __restrict__ vout, int n, int shift,
+    const unsigned* __restrict__ offsets, int n_tiles) {
+  constexpr int kWarps = kSortThreads / 32;
+  __shared__ unsigned base_off[256];
+  __shared__ unsigned wcnt[kWarps][256];
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  for (int d = threadIdx.x; d < 256; d += blockDim.x)
+    base_off[d] = offsets[(size_t)d * n_tiles + blockIdx.x];
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const int base = blockIdx.x * kSortTile;
+  for (int r = 0; r < kSortItems; ++r) {
+    for (int d = lane; d < 256; d += 32) wcnt[warp][d] = 0;
+    __syncthreads();
+    const int i = base + r * kSortThreads + threadIdx.x;
+    const bool valid = i < n;
+    unsigned long long k = valid ? kin[i] : 0ull;
+    unsigned v = valid ? vin[i] : 0u;
+    unsigned digit = valid ? ((unsigned)(k >> shift) & 255u) : 256u;
+    unsigned peers = __match_any_sync(0xffffffffu, digit);
+    unsigned rank = __popc(peers & lt_mask);
+    if (valid && rank == 0) wcnt[warp][digit] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      unsigned pos = base_off[digit] + rank;
+      for (unsigned w = 0; w < warp; ++w) pos += wcnt[w][digit];
+      kout[pos] = k;
+      vout[pos] = v;
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+      unsigned t = 0;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) t += wcnt[w][d];
+      base_off[d] += t;
+    }
+    __syncthreads();
+  }
+}
+
+struct SortScratch {
+  unsigned long long* k2;
+  unsigned* v2;
+  unsigned* counts;
+  unsigned* scan_scratch;
+};
+
+static size_t sort_count_words(int n) {
+  int tiles = (n + kSortTile - 1) / kSortTile;
+  return (size_t)256 * (size_t)(tiles > 0 ? tiles : 1);
+}
+
+// Sorts (k, v) by bits [0, bits) of k; result ends in (k, v). Uses the scratch buffers.
+static void radix_sort(unsigned long long* k, unsigned* v, int n, int bits, const SortScratch& S,
+                       cudaStream_t s) {
+  if (n <= 1) return;
+  const int tiles = (n + kSortTile - 1) / kSortTile;
+  const int nc = 256 * tiles;
+  unsigned long long *ka = k, *kb = S.k2;
+  unsigned *va = v, *vb = S.v2;
+  int passes = (bits + 7) / 8;
+  for (int p = 0; p < passes; ++p) {
+    int shift = 8 * p;
+    radix_hist_kernel<<<tiles, kSortThreads, 0, s>>>(ka, n, shift, S.counts, tiles);
+    note_launch();
+    exclusive_scan(S.counts, nc, S.scan_scratch, s);
+    radix_scatter_kernel<<<tiles, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shift, S.counts, tiles);
+    note_launch();
+    unsigned long long* tk = ka;
+    ka = kb;
+    kb = tk;
+    unsigned* tv = va;
+    va = vb;
+    vb = tv;
+  }
+  if (ka != k) {
+    cudaMemcpyAsync(k, ka, (size_t)n * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(v, va, (size_t)n * sizeof(unsigned), cudaMemcpyDeviceToDevice, s);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Particle gather into Morton order
+// ------------------------------------------------------------------------------------
+__global__ void gather_particles_kernel(const float* __restrict__ xyz,
+                                        const float* __restrict__ alpha,
+                                        const float* __restrict__ weight, int n,
+                                        const unsigned* __restrict__ order, float4* pos, float* w,
+                                        int* perm, int* rank) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int o = (int)order[i];
+  pos[i] = make_float4(xyz[o], xyz[(size_t)n + o], xyz[2 * (size_t)n + o], alpha[o]);
+  w[i] = weight ? weight[o] : 1.0f;
+  perm[i] = o;
+  rank[o] = i;
+}
+
+// ------------------------------------------------------------------------------------
+// Topology: top-down, one level per pair of launches
+// ------------------------------------------------------------------------------------
+constexpr int kTopoBlocks = 512;
+constexpr int kTopoThreads = 256;
+
+struct TopoArrays {
+  const unsigned long long* key;
+  int* nfirst;
+  int* ncount;
+  int4* nglo;  // w = split axis (-1 leaf)
+  int4* nghi;
+  int4* nT;    // x child, y parent, z src_first, w src_count
+  int* ndepth;
+  int* nsplit;  // first particle of the upper child, -1 for a leaf
+  int* nbit;    // split key bit
+  int* leaf_of;
+  int* levels;  // [kMaxLevels][2]
+  unsigned* bcount;  // [kTopoBlocks]
+  int bucket;
+};
+
+__global__ void topo_init_kernel(TopoArrays A, int n) {
+  for (int l = threadIdx.x; l < 2 * kMaxLevels; l += blockDim.x) A.levels[l] = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    A.levels[0] = kRoot;
+    A.levels[1] = kRoot + 1;
+    A.nfirst[kRoot] = 0;
+    A.ncount[kRoot] = n;
+    A.nglo[kRoot] = make_int4(0, 0, 0, -1);
+    A.nghi[kRoot] = make_int4(kGridMax, kGridMax, kGridMax, 0);
+    A.nT[kRoot] = make_int4(-1, 0, 0, 0);
+    A.ndepth[kRoot] = 0;
+    // entry 0 is unused: make it an inert leaf
+    A.nT[0] = make_int4(-1, 0, 0, 0);
+  }
+}
+
+__device__ __forceinline__ void level_chunk(const int* levels, int L, int* begin, int* end,
+                                            int* c0, int* c1) {
+  *begin = levels[2 * L];
+  *end = levels[2 * L + 1];
+  int m = *end - *begin;
+  int chunk = (m + gridDim.x - 1) / gridDim.x;
+  *c0 = *begin + blockIdx.x * chunk;
+  *c1 = min(*c0 + chunk, *end);
+}
+
+// Decide leaf / split for every cell of level L; count internal cells per block.
+__global__ void __launch_bounds__(kTopoThreads) topo_split_kernel(TopoArrays A, int L) {
+  __shared__ unsigned long long red[32];
+  int begin, end, c0, c1;
+  level_chunk(A.levels, L, &begin, &end, &c0, &c1);
+  unsigned long long cnt = 0;
+  for (int X = c0 + threadIdx.x; X < c1; X += blockDim.x) {
+    const int f = A.nfirst[X], c = A.ncount[X];
+    const unsigned long long kf = A.key[f], kl = A.key[f + c - 1];
+    if (c <= A.bucket || kf == kl) {
+      A.nsplit[X] = -1;
+      A.nT[X].x = -1;
+      A.nglo[X].w = -1;
+      for (int i = f; i < f + c; ++i) A.leaf_of[i] = X;
+    } else {
+      const int b = 63 - __clzll((long long)(kf ^ kl));
+      // first index in [f, f+c) whose key has bit b set (bit b is monotone in the range)
+      int lo = f, hi = f + c - 1;
+      while (lo < hi) {
+        int mid = lo + ((hi - lo) >> 1);
+        if ((A.key[mid] >> b) & 1ull) hi = mid;
+        else lo = mid + 1;
+      }
+      A.nsplit[X] = lo;
+      A.nbit[X] = b;
+      ++cnt;
+    }
+  }
+  unsigned long long tot = block_reduce_add(cnt, red);
+  if (threadIdx.x == 0) A.bcount[blockIdx.x] = (unsigned)tot;
+}
+
+// Allocate the children of the internal cells of level L (in cell order, two
+// consecutive slots each) and write their ranges and boxes.
+__global__ void __launch_bounds__(kTopoThreads) topo_emit_kernel(TopoArrays A, int L) {
+  __shared__ unsigned scan_smem[32];
+  __shared__ unsigned long long red[32];
+  int begin, end, c0, c1;
+  level_chunk(A.levels, L, &begin, &end, &c0, &c1);
+  // offset of this block = sum of the counts of the blocks before it
+  unsigned long long pre = 0, all = 0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    unsigned v = A.bcount[b];
+    all += v;
+    if (b < (int)blockIdx.x) pre += v;
+  }
+  pre = block_reduce_add(pre, red);
+  all = block_reduce_add(all, red);
+  __shared__ unsigned s_pre;
+  if (threadIdx.x == 0) {
+    s_pre = (unsigned)pre;
+    if (blockIdx.x == 0) {
+      A.levels[2 * (L + 1)] = end;
+      A.levels[2 * (L + 1) + 1] = end + 2 * (int)all;
+    }
+  }
+  __syncthreads();
+  unsigned running = s_pre;
+  for (int base = c0; base < c1; base += blockDim.x) {
+    const int X = base + threadIdx.x;
+    const bool internal = X < c1 && A.nsplit[X] >= 0;
+    unsigned total;
+    unsigned off = block_exclusive_scan(internal ? 1u : 0u, scan_smem, &total);
+    if (internal) {
+      const int child = end + 2 * (int)(running + off);
+      const int f = A.nfirst[X], c = A.ncount[X], k = A.nsplit[X], b = A.nbit[X];
+      const int axis = (62 - b) % 3;
+      const int shift = kGridBits - 1 - (62 - b) / 3;
+      const unsigned g = key_coord(A.key[f], axis);
+      const int plane = (int)(((g >> shift) | 1u) << shift);
+      int4 lo = A.nglo[X], hi = A.nghi[X];
+      A.nT[X].x = child;
+      A.nglo[X].w = axis;
+      int4 lo1 = make_int4(lo.x, lo.y, lo.z, 0), hi1 = make_int4(hi.x, hi.y, hi.z, 0);
+      int4 lo2 = lo1, hi2 = hi1;
+      if (axis == 0) { hi1.x = plane; lo2.x = plane; }
+      else if (axis == 1) { hi1.y = plane; lo2.y = plane; }
+      else { hi1.z = plane; lo2.z = plane; }
+      A.nfirst[child] = f;
+      A.ncount[child] = k - f;
+      A.nfirst[child + 1] = k;
+      A.ncount[child + 1] = f + c - k;
+      A.nglo[child] = lo1;
+      A.nghi[child] = hi1;
+      A.nglo[child + 1] = lo2;
+      A.nghi[child + 1] = hi2;
+      A.nT[child] = make_int4(-1, X, 0, 0);
+      A.nT[child + 1] = make_int4(-1, X, 0, 0);
+      A.ndepth[child] = L + 1;
+      A.ndepth[child + 1] = L + 1;
+    }
+    running += total;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Sources: leaf of each source (descend by the cut planes), sort, ranges
+// ------------------------------------------------------------------------------------
+__global__ void src_leaf_kernel(const float* __restrict__ xyz, const float* __restrict__ lum,
+                                int n_src, Domain32 D, const int4* __restrict__ nT,
+                                const int4* __restrict__ nglo, const int* __restrict__ nfirst,
+                                unsigned long long* keys, unsigned* vals, int* status) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_src) return;
+  float x = xyz[s], y = xyz[(size_t)n_src + s], z = xyz[2 * (size_t)n_src + s];
+  float L = lum[s];
+  if (!(L >= 0.0f) || !isfinite(L)) atomicOr(status, kStatusInvalid);
+  if (!(in_dom(x, D.lo[0], D.hi[0]) && in_dom(y, D.lo[1], D.hi[1]) &&
+        in_dom(z, D.lo[2], D.hi[2]))) {
+    atomicOr(status, kStatusOutOfDomain);
+    keys[s] = 0;
+    vals[s] = (unsigned)s;
+    return;
+  }
+  int g[3] = {(int)quantize(x, D.lo[0], D.scale), (int)quantize(y, D.lo[1], D.scale),
+              (int)quantize(z, D.lo[2], D.scale)};
+  int X = kRoot;
+  for (int it = 0; it < kMaxLevels; ++it) {
+    int child = nT[X].x;
+    if (child < 0) break;
+    int a = nglo[X].w;
+    int4 up = nglo[child + 1];
+    int plane = a == 0 ? up.x : (a == 1 ? up.y : up.z);
+    X = g[a] >= plane ? child + 1 : child;
+  }
+  keys[s] = (unsigned long long)nfirst[X];
+  vals[s] = (unsigned)s;
+}
+
+__global__ void gather_sources_kernel(const float* __restrict__ xyz, const float* __restrict__ lum,
+                                      int n_src, const unsigned* __restrict__ order, float4* src,
+                                      int* src_order) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_src) return;
+  int o = (int)order[k];
+  src[k] = make_float4(xyz[o], xyz[(size_t)n_src + o], xyz[2 * (size_t)n_src + o], lum[o]);
+  src_order[k] = o;
+}
+
+__device__ __forceinline__ int lower_bound_u64(const unsigned long long* a, int n,
+                                               unsigned long long v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int m = lo + ((hi - lo) >> 1);
+    if (a[m] < v) lo = m + 1;
+    else hi = m;
+  }
+  return lo;
+}
+
+__global__ void node_src_range_kernel(int n_cells_end, const int* __restrict__ nfirst,
+                                      const int* __restrict__ ncount,
+                                      const unsigned long long* __restrict__ src_keys, int n_src,
+                                      int4* nT) {
+  int X = blockIdx.x * blockDim.x + threadIdx.x + kRoot;
+  if (X >= n_cells_end) return;
+  int a = lower_bound_u64(src_keys, n_src, (unsigned long long)nfirst[X]);
+  int b = lower_bound_u64(src_keys, n_src, (unsigned long long)(nfirst[X] + ncount[X]));
+  nT[X].z = a;
+  nT[X].w = b - a;
+}
+
+// ------------------------------------------------------------------------------------
+// Cell moments, bottom-up one level per launch. FP64 sums; explicit round-to-nearest
+// operations so that no multiply-add is contracted and the directional
+// alpha_min/alpha_max follow the same operation order as their definition.
+// ------------------------------------------------------------------------------------
+struct Moments {
+  double W, WA, L, LY[3], amin[3], amax[3];
+};
+
+struct MomentArrays {
+  const int4* nT;
+  const int4* nglo;
+  const int4* nghi;
+  const int* nfirst;
+  const int* ncount;
+  const float4* pos;
+  const float* w;
+  const float4* src;
+  const int* levels;
+  Moments* mom;
+  float4* nA;
+  float4* nB;
+  float4* nS;
+  float* nl2;
+  float lo[3], h;
+};
+
+__device__ __forceinline__ float world(float lo, float h, int g) {
+  return __fadd_rn(lo, __fmul_rn((float)g, h));
+}
+
+__global__ void moments_level_kernel(MomentArrays A, int L) {
+  const int begin = A.levels[2 * L], end = A.levels[2 * L + 1];
+  for (int X = begin + blockIdx.x * blockDim.x + threadIdx.x; X < end;
+       X += gridDim.x * blockDim.x) {
+    const int4 t = A.nT[X];
+    Moments m;
+    if (t.x < 0) {
+      double sw = 0.0, swa = 0.0;
+      const int f = A.nfirst[X], c = A.ncount[X];
+      for (int i = f; i < f + c; ++i) {
+        double wi = (double)A.w[i];
+        sw = __dadd_rn(sw, wi);
+        swa = __dadd_rn(swa, __dmul_rn(wi, (double)A.pos[i].w));
+      }
+      double sl = 0.0, sy0 = 0.0, sy1 = 0.0, sy2 = 0.0;
+      for (int s = t.z; s < t.z + t.w; ++s) {
+        float4 y = A.src[s];
+        double Lj = (double)y.w;
+        sl = __dadd_rn(sl, Lj);
+        sy0 = __dadd_rn(sy0, __dmul_rn(Lj, (double)y.x));
+        sy1 = __dadd_rn(sy1, __dmul_rn(Lj, (double)y.y));
+        sy2 = __dadd_rn(sy2, __dmul_rn(Lj, (double)y.z));
+      }
+      m.W = sw;
+      m.WA = swa;
+      m.L = sl;
+      m.LY[0] = sy0;
+      m.LY[1] = sy1;
+      m.LY[2] = sy2;
+      const double ab = __ddiv_rn(swa, sw);
+      for (int d = 0; d < 3; ++d) m.amin[d] = m.amax[d] = ab;
+    } else {
+      const Moments& m1 = A.mom[t.x];
+      const Moments& m2 = A.mom[t.x + 1];
+      m.W = __dadd_rn(m1.W, m2.W);
+      m.WA = __dadd_rn(m1.WA, m2.WA);
+      m.L = __dadd_rn(m1.L, m2.L);
+      for (int d = 0; d < 3; ++d) m.LY[d] = __dadd_rn(m1.LY[d], m2.LY[d]);
+      const int a = A.nglo[X].w;
+      const int4 l1 = A.nglo[t.x], h1 = A.nghi[t.x], l2 = A.nglo[t.x + 1], h2 = A.nghi[t.x + 1];
+      const int4 lX = A.nglo[X], hX = A.nghi[X];
+      const int lo1[3] = {l1.x, l1.y, l1.z}, hi1[3] = {h1.x, h1.y, h1.z};
+      const int lo2[3] = {l2.x, l2.y, l2.z}, hi2[3] = {h2.x, h2.y, h2.z};
+      const int loX[3] = {lX.x, lX.y, lX.z}, hiX[3] = {hX.x, hX.y, hX.z};
+      for (int d = 0; d < 3; ++d) {
+        if (d == a) {
+          // the ray crosses both children: optical depths add, divide by the width
+          const double w1 = (double)(hi1[d] - lo1[d]);
+          const double w2 = (double)(hi2[d] - lo2[d]);
+          const double Wd = (double)(hiX[d] - loX[d]);
+          m.amin[d] = __ddiv_rn(__dadd_rn(__dmul_rn(m1.amin[d], w1), __dmul_rn(m2.amin[d], w2)), Wd);
+          m.amax[d] = __ddiv_rn(__dadd_rn(__dmul_rn(m1.amax[d], w1), __dmul_rn(m2.amax[d], w2)), Wd);
+        } else {
+          // one child or the other
+          m.amin[d] = fmin(m1.amin[d], m2.amin[d]);
+          m.amax[d] = fmax(m1.amax[d], m2.amax[d]);
+        }
+      }
+    }
+    A.mom[X] = m;
+    const double amin = fmin(fmin(m.amin[0], m.amin[1]), m.amin[2]);
+    const double amax = fmax(fmax(m.amax[0], m.amax[1]), m.amax[2]);
+    const float abar = __double2float_rn(__ddiv_rn(m.WA, m.W));
+    const float dal = __double2float_rn(__dsub_rn(amax, amin));
+    const float Lf = __double2float_rn(m.L);
+    float c[3];
+    for (int d = 0; d < 3; ++d) c[d] = m.L > 0.0 ? __double2float_rn(__ddiv_rn(m.LY[d], m.L)) : 0.0f;
+    const int4 gl = A.nglo[X], gh = A.nghi[X];
+    const float blo[3] = {world(A.lo[0], A.h, gl.x), world(A.lo[1], A.h, gl.y),
+                          world(A.lo[2], A.h, gl.z)};
+    const float bhi[3] = {world(A.lo[0], A.h, gh.x), world(A.lo[1], A.h, gh.y),
+                          world(A.lo[2], A.h, gh.z)};
+    float l2 = 0.0f;
+    for (int d = 0; d < 3; ++d) {
+      float e = fmaxf(__fsub_rn(c[d], blo[d]), __fsub_rn(bhi[d], c[d]));
+      l2 = __fadd_rn(l2, __fmul_rn(e, e));
+    }
+    A.nA[X] = make_float4(blo[0], blo[1], blo[2], abar);
+    A.nB[X] = make_float4(bhi[0], bhi[1], bhi[2], dal);
+    A.nS[X] = make_float4(c[0], c[1], c[2], Lf);
+    A.nl2[X] = l2;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Host driver
+// ------------------------------------------------------------------------------------
+namespace {
+
+struct Allocs {
+  std::vector<void*> ptrs;
+  cudaStream_t s;
+  bool ok = true;
+  template <class T>
+  T* get(size_t n) {
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, (n ? n : 1) * sizeof(T), s) != cudaSuccess) {
+      ok = false;
+      return nullptr;
+    }
+    ptrs.push_back(p);
+    return (T*)p;
+  }
+  void release() {
+    for (void* p : ptrs) cudaFreeAsync(p, s);
+    ptrs.clear();
+  }
+};
+
+inline int grid_for(long long n, int threads) { return (int)((n + threads - 1) / threads); }
+
+}  // namespace
+
+TreeView trevr_tree_view(const trevr_tree* t);
+
+int build_tree_impl(const float* gas_xyz, const float* alpha, const float* weight, long long n_gas_ll,
+                    const float* src_xyz, const float* src_lum, long long n_src_ll,
+                    const trevr_domain* dom, int bucket, cudaStream_t s, trevr_tree** out,
+                    float* build_ms) {
+  const int n = (int)n_gas_ll;
+  const int ns = (int)n_src_ll;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+
+  trevr_tree* t = new trevr_tree();
+  std::memset(t, 0, sizeof(*t));
+  cudaGetDevice(&t->device);
+  t->n_gas = n;
+  t->n_src = ns;
+  t->bucket = bucket;
+  for (int d = 0; d < 3; ++d) t->lo[d] = dom->lo[d];
+  t->side = dom->side;
+  {
+    volatile float side = dom->side;  // fp32 on the host, as on the device
+    t->h = side * (1.0f / 2097152.0f);
+  }
+  const size_t cap = 2 * (size_t)n + 2;
+  t->cap_nodes = cap;
+
+  Allocs keep{{}, s}, tmp{{}, s};
+  // persistent
+  t->key = keep.get<unsigned long long>(n);
+  t->perm = keep.get<int>(n);
+  t->rank = keep.get<int>(n);
+  t->leaf_of = keep.get<int>(n);
+  t->pos = keep.get<float4>(n);
+  t->w = keep.get<float>(n);
+  t->nfirst = keep.get<int>(cap);
+  t->ncount = keep.get<int>(cap);
+  t->nglo = keep.get<int4>(cap);
+  t->nghi = keep.get<int4>(cap);
+  t->nT = keep.get<int4>(cap);
+  t->ndepth = keep.get<int>(cap);
+  t->src = keep.get<float4>(ns);
+  t->src_order = keep.get<int>(ns);
+  t->levels = keep.get<int>(2 * kMaxLevels);
+  t->d_n_nodes = keep.get<int>(1);
+  t->status = keep.get<int>(1);
+  t->d_stats = keep.get<unsigned long long>(8);
+  // scratch
+  unsigned* vals = tmp.get<unsigned>(n);
+  const int nmax = n > ns ? n : ns;
+  SortScratch SS;
+  SS.k2 = tmp.get<unsigned long long>(nmax);
+  SS.v2 = tmp.get<unsigned>(nmax);
+  SS.counts = tmp.get<unsigned>(sort_count_words(nmax));
+  SS.scan_scratch = tmp.get<unsigned>(scan_scratch_words((int)sort_count_words(nmax)));
+  int* nsplit = tmp.get<int>(cap);
+  int* nbit = tmp.get<int>(cap);
+  unsigned* bcount = tmp.get<unsigned>(kTopoBlocks);
+  unsigned long long* skeys = tmp.get<unsigned long long>(ns);
+  unsigned* svals = tmp.get<unsigned>(ns);
+
+  auto fail = [&](int code) {
+    tmp.release();
+    keep.release();
+    cudaStreamSynchronize(s);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    delete t;
+    return code;
+  };
+  if (!keep.ok || !tmp.ok) {
+    cudaGetLastError();
+    return fail(TREVR_ERR_OUT_OF_MEMORY);
+  }
+  cudaMemsetAsync(t->status, 0, sizeof(int), s);
+  cudaMemsetAsync(t->d_stats, 0, 8 * sizeof(unsigned long long), s);
+
+  Domain32 D;
+  for (int d = 0; d < 3; ++d) {
+    volatile float lo = dom->lo[d], side = dom->side;
+    D.lo[d] = lo;
+    D.hi[d] = lo + side;
+  }
+  {
+    volatile float side = dom->side;
+    D.scale = 2097152.0f / side;
+  }
+  D.h = t->h;
+
+  // 1. keys and sort
+  keys_kernel<<<grid_for(n, 256), 256, 0, s>>>(gas_xyz, alpha, weight, n, D, t->key, vals,
+                                                 t->status);
+  note_launch();
+  radix_sort(t->key, vals, n, 63, SS, s);
+  gather_particles_kernel<<<grid_for(n, 256), 256, 0, s>>>(gas_xyz, alpha, weight, n, vals,
+                                                            t->pos, t->w, t->perm, t->rank);
+  note_launch();
+  // 2. topology, top-down
+  TopoArrays TA;
+  TA.key = t->key;
+  TA.nfirst = t->nfirst;
+  TA.ncount = t->ncount;
+  TA.nglo = t->nglo;
+  TA.nghi = t->nghi;
+  TA.nT = t->nT;
+  TA.ndepth = t->ndepth;
+  TA.nsplit = nsplit;
+  TA.nbit = nbit;
+  TA.leaf_of = t->leaf_of;
+  TA.levels = t->levels;
+  TA.bcount = bcount;
+  TA.bucket = bucket;
+  topo_init_kernel<<<1, 128, 0, s>>>(TA, n);
+  note_launch();
+  for (int L = 0; L < kMaxLevels - 1; ++L) {
+    topo_split_kernel<<<kTopoBlocks, kTopoThreads, 0, s>>>(TA, L);
+    note_launch();
+    topo_emit_kernel<<<kTopoBlocks, kTopoThreads, 0, s>>>(TA, L);
+    note_launch();
+  }
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return fail(cuda_to_error(err));
+  int levels[2 * kMaxLevels];
+  cudaMemcpyAsync(levels, t->levels, sizeof(levels), cudaMemcpyDeviceToHost, s);
+  err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) return fail(cuda_to_error(err));
+  int max_depth = 0;
+  for (int L = 0; L < kMaxLevels; ++L)
+    if (levels[2 * L + 1] > levels[2 * L]) max_depth = L;
+  const int end_cells = levels[2 * max_depth + 1];
+  t->n_nodes = end_cells - kRoot;
+  t->max_depth = max_depth;
+
+  // 3. sources
+  if (ns > 0) {
+    src_leaf_kernel<<<grid_for(ns, 256), 256, 0, s>>>(src_xyz, src_lum, ns, D, t->nT, t->nglo,
+                                                       t->nfirst, skeys, svals, t->status);
+    note_launch();
+    radix_sort(skeys, svals, ns, 32, SS, s);
+    gather_sources_kernel<<<grid_for(ns, 256), 256, 0, s>>>(src_xyz, src_lum, ns, svals, t->src,
+                                                             t->src_order);
+    note_launch();
+    node_src_range_kernel<<<grid_for(end_cells - kRoot, 256), 256, 0, s>>>(
+        end_cells, t->nfirst, t->ncount, skeys, ns, t->nT);
+    note_launch();
+  }
+  // 4. moments, bottom-up
+  const size_t ncell = (size_t)end_cells;
+  t->nA = keep.get<float4>(ncell);
+  t->nB = keep.get<float4>(ncell);
+  t->nS = keep.get<float4>(ncell);
+  t->nl2 = keep.get<float>(ncell);
+  Moments* mom = tmp.get<Moments>(ncell);
+  if (!keep.ok || !tmp.ok) {
+    cudaGetLastError();
+    return fail(TREVR_ERR_OUT_OF_MEMORY);
+  }
+  // entry 0: an inert cell (no luminosity)
+  cudaMemsetAsync(t->nA, 0, sizeof(float4), s);
+  cudaMemsetAsync(t->nB, 0, sizeof(float4), s);
+  cudaMemsetAsync(t->nS, 0, sizeof(float4), s);
+  cudaMemsetAsync(t->nl2, 0, sizeof(float), s);
+  MomentArrays MA;
+  MA.nT = t->nT;
+  MA.nglo = t->nglo;
+  MA.nghi = t->nghi;
+  MA.nfirst = t->nfirst;
+  MA.ncount = t->ncount;
+  MA.pos = t->pos;
+  MA.w = t->w;
+  MA.src = t->src;
+  MA.levels = t->levels;
+  MA.mom = mom;
+  MA.nA = t->nA;
+  MA.nB = t->nB;
+  MA.nS = t->nS;
+  MA.nl2 = t->nl2;
+  for (int d = 0; d < 3; ++d) MA.lo[d] = t->lo[d];
+  MA.h = t->h;
+  for (int L = max_depth; L >= 0; --L) {
+    int m = levels[2 * L + 1] - levels[2 * L];
+    int blocks = grid_for(m, 128);
+    if (blocks > 4096) blocks = 4096;
+    moments_level_kernel<<<blocks, 128, 0, s>>>(MA, L);
+    note_launch();
+  }
+  cudaMemcpyAsync(t->d_n_nodes, &levels[2 * max_depth + 1], sizeof(int), cudaMemcpyHostToDevice, s);
+  tmp.release();
+  cudaEventRecord(e1, s);
+  int status = 0;
+  cudaMemcpyAsync(&status, t->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  err = cudaStreamSynchronize(s);
+  if (err == cudaSuccess) err = cudaGetLastError();
+  if (err != cudaSuccess) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    keep.release();
+    delete t;
+    return cuda_to_error(err);
+  }
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  if (build_ms) *build_ms = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (status) {
+    keep.release();
+    cudaStreamSynchronize(s);
+    delete t;
+    return status_to_error(status);
+  }
+  // keep.ptrs is dropped: the tree owns those buffers now
+  *out = t;
+  return TREVR_OK;
+}
+
+}  // namespace trevr

@@ -1,0 +1,115 @@
+// Internal declarations shared by the CUDA translation units of libtrevr.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "trevr.h"
+
+namespace trevr {
+
+constexpr int kGridBits = 21;
+constexpr int kGridMax = 1 << kGridBits;  // cells per axis of the integer grid
+constexpr int kRoot = 1;                  // breadth-first numbering, root at 1
+constexpr int kMaxLevels = 66;            // depth <= 63 (one key bit per cut), plus slack
+constexpr int kDefaultStack = 64;         // >= max depth + 1: a walk can never overflow it
+constexpr int kMaxStack = 128;
+
+// device status bits (OR-ed by kernels, mapped to TREVR_ERR_* on the host)
+constexpr int kStatusOutOfDomain = 1;
+constexpr int kStatusInvalid = 2;
+constexpr int kStatusStackOverflow = 4;
+constexpr int kStatusIterationLimit = 8;
+
+// Device-side view of a built tree (all pointers are device memory).
+struct TreeView {
+  int n_gas, n_src, n_nodes_cap;
+  int bucket;
+  float lo[3], side, h;
+  // particles, Morton order
+  const unsigned long long* key;
+  const int* perm;     // sorted -> caller
+  const int* rank;     // caller -> sorted
+  const int* leaf_of;  // sorted -> leaf cell
+  const float4* pos;   // (x, y, z, alpha), sorted
+  const float* w;      // sorted weights
+  // cells, breadth-first numbering (root = 1, children 2k, 2k+1)
+  const float4* nA;  // (lo.x, lo.y, lo.z, abar)
+  const float4* nB;  // (hi.x, hi.y, hi.z, alpha_max - alpha_min)
+  const float4* nS;  // (cen.x, cen.y, cen.z, L)
+  const int4* nT;    // (child or -1, parent, src_first, src_count)
+  const float* nl2;  // l^2 (furthest vertex from the centre of luminosity)
+  const int* ndepth;
+  const int* nfirst;
+  const int* ncount;
+  // sources sorted by the first particle of their leaf
+  const float4* src;  // (y.x, y.y, y.z, L)
+  const int* src_order;
+  const int* n_nodes;  // device scalar
+};
+
+}  // namespace trevr
+
+// Host-side tree object behind the opaque C handle.
+struct trevr_tree {
+  int device;
+  long long n_gas, n_src, n_nodes;
+  int max_depth;
+  int bucket;
+  float lo[3], side, h;
+  size_t cap_nodes;
+  // particles
+  unsigned long long* key;
+  int* perm;
+  int* rank;
+  int* leaf_of;
+  float4* pos;
+  float* w;
+  // cells
+  float4* nA;
+  float4* nB;
+  float4* nS;
+  int4* nT;
+  float* nl2;
+  int* ndepth;
+  int* nfirst;
+  int* ncount;
+  int4* nglo;  // (x, y, z, split axis or -1)
+  int4* nghi;
+  // sources
+  float4* src;
+  int* src_order;
+  // bookkeeping
+  int* levels;    // kMaxLevels x 2 (begin, end)
+  int* d_n_nodes;
+  int* status;    // device status word
+  unsigned long long* d_stats;  // 4 counters
+  trevr::TreeView view() const;
+};
+
+namespace trevr {
+
+// ---- build.cu
+int build_tree_impl(const float* gas_xyz, const float* alpha, const float* weight, long long n_gas,
+                    const float* src_xyz, const float* src_lum, long long n_src,
+                    const trevr_domain* dom, int bucket, cudaStream_t s, trevr_tree** out,
+                    float* build_ms);
+
+// ---- walk.cu
+struct WalkParams {
+  float theta2;  // theta_open^2 (fp32)
+  float tau_ref;
+  float smin2;   // (1e-12 side)^2 (fp32): coincident-source cut
+  int stack_depth;
+};
+cudaError_t launch_walk(const TreeView& T, const long long* sink_idx, int n_sink,
+                        const WalkParams& wp, float* flux_out, int* counters,
+                        unsigned long long* stats, int* status, int block_size,
+                        cudaStream_t s);
+
+// ---- api.cu helpers
+int status_to_error(int status_bits);
+void note_launch(int n = 1);  // count kernels launched by the library
+int cuda_to_error(cudaError_t e);
+
+}  // namespace trevr

@@ -1,0 +1,244 @@
+"""Python binding of libtrevr (include/trevr.h): argument marshalling only.
+
+Every step of the hot path runs in the CUDA library; this module passes
+device pointers of torch tensors and the current CUDA stream through ctypes.
+There is no CPU fallback: if libtrevr.so is missing or no GPU is present the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtrevr.so")
+
+TREVR_OK = 0
+ERRORS = {
+    1: "TREVR_ERR_INVALID_ARGUMENT",
+    2: "TREVR_ERR_OUT_OF_DOMAIN",
+    3: "TREVR_ERR_STACK_OVERFLOW",
+    4: "TREVR_ERR_ITERATION_LIMIT",
+    5: "TREVR_ERR_CUDA",
+    6: "TREVR_ERR_OUT_OF_MEMORY",
+}
+
+# names of every entry point declared in include/trevr.h
+EXPORTS = (
+    "trevr_build_tree", "trevr_compute_flux", "trevr_check", "trevr_tree_info",
+    "trevr_tree_export", "trevr_tree_free", "trevr_status_string", "trevr_kernel_launches",
+)
+
+
+class TrevrError(RuntimeError):
+    def __init__(self, code, where=""):
+        name = ERRORS.get(code, f"code {code}")
+        super().__init__(f"{where}: {name}" if where else name)
+        self.code = code
+
+
+class Domain(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_float * 3), ("side", ctypes.c_float)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("theta_open", ctypes.c_float), ("tau_ref", ctypes.c_float),
+                ("bucket", ctypes.c_int), ("sinks_per_warp", ctypes.c_int),
+                ("block_size", ctypes.c_int), ("stack_depth", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("interactions", ctypes.c_longlong), ("segments", ctypes.c_longlong),
+                ("src_nodes_visited", ctypes.c_longlong),
+                ("refine_expansions", ctypes.c_longlong), ("cells_clipped", ctypes.c_longlong),
+                ("build_ms", ctypes.c_float),
+                ("walk_ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libtrevr.so and declare its signatures (raises if it is not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is not built; run paper_1902_08083_gb300._build.build()")
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        ll = ctypes.c_longlong
+        lib.trevr_build_tree.argtypes = [P, P, P, ll, P, P, ll, ctypes.POINTER(Domain),
+                                         ctypes.POINTER(Params), P, ctypes.POINTER(P)]
+        lib.trevr_build_tree.restype = ctypes.c_int
+        lib.trevr_compute_flux.argtypes = [P, P, ll, ctypes.POINTER(Params), P, P,
+                                           ctypes.POINTER(Stats), P]
+        lib.trevr_compute_flux.restype = ctypes.c_int
+        lib.trevr_check.argtypes = [P, P]
+        lib.trevr_check.restype = ctypes.c_int
+        lib.trevr_tree_info.argtypes = [P, ctypes.POINTER(ll), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ll), ctypes.POINTER(ll)]
+        lib.trevr_tree_info.restype = ctypes.c_int
+        lib.trevr_tree_export.argtypes = [P] * 20
+        lib.trevr_tree_export.restype = ctypes.c_int
+        lib.trevr_tree_free.argtypes = [P]
+        lib.trevr_tree_free.restype = None
+        lib.trevr_kernel_launches.argtypes = []
+        lib.trevr_kernel_launches.restype = ctypes.c_ulonglong
+        lib.trevr_status_string.argtypes = [ctypes.c_int]
+        lib.trevr_status_string.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _dev_ptr(t, dtype, name):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_params(theta=0.75, tau_ref=0.1, bucket=8, sinks_per_warp=0, block_size=0,
+                stack_depth=0):
+    return Params(float(theta), float(tau_ref), int(bucket), int(sinks_per_warp),
+                  int(block_size), int(stack_depth))
+
+
+class Tree:
+    """A radiation tree built on the GPU (trevr_build_tree); owns the C handle."""
+
+    def __init__(self, gas_xyz, alpha, src_xyz, src_lum, weight=None, lo=(0.0, 0.0, 0.0),
+                 side=1.0, bucket=8, stream=None):
+        lib = load_library()
+        self._lib = lib
+        self._h = None
+        gas_xyz = gas_xyz.contiguous()
+        src_xyz = src_xyz.contiguous()
+        if gas_xyz.dim() != 2 or gas_xyz.shape[0] != 3:
+            raise ValueError("gas_xyz must have shape (3, N)")
+        if src_xyz.dim() != 2 or src_xyz.shape[0] != 3:
+            raise ValueError("src_xyz must have shape (3, S)")
+        self.n_gas = int(gas_xyz.shape[1])
+        self.n_src = int(src_xyz.shape[1])
+        self.device = gas_xyz.device
+        dom = Domain((ctypes.c_float * 3)(*[float(v) for v in lo]), float(side))
+        prm = make_params(bucket=bucket)
+        h = ctypes.c_void_p()
+        rc = lib.trevr_build_tree(
+            _dev_ptr(gas_xyz, torch.float32, "gas_xyz"), _dev_ptr(alpha, torch.float32, "alpha"),
+            _dev_ptr(weight, torch.float32, "weight"), self.n_gas,
+            _dev_ptr(src_xyz, torch.float32, "src_xyz") if self.n_src else None,
+            _dev_ptr(src_lum, torch.float32, "src_lum") if self.n_src else None, self.n_src,
+            ctypes.byref(dom), ctypes.byref(prm), _stream_ptr(stream), ctypes.byref(h))
+        if rc != TREVR_OK:
+            raise TrevrError(rc, "trevr_build_tree")
+        self._h = h
+        self.bucket = bucket
+        self.side = float(side)
+        nn = ctypes.c_longlong()
+        md = ctypes.c_int()
+        lib.trevr_tree_info(h, ctypes.byref(nn), ctypes.byref(md), None, None)
+        self.n_nodes = nn.value
+        self.max_depth = md.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            self._lib.trevr_tree_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def export(self, stream=None):
+        """Copy the tree into torch tensors on the tree's device (see trevr_tree_export)."""
+        dev = self.device
+        n, nc, ns = self.n_gas, self.n_nodes + 1, self.n_src
+        i32 = dict(dtype=torch.int32, device=dev)
+        f32 = dict(dtype=torch.float32, device=dev)
+        out = dict(key=torch.empty(n, dtype=torch.int64, device=dev),
+                   perm=torch.empty(n, **i32), leaf_of=torch.empty(n, **i32),
+                   first=torch.empty(nc, **i32), count=torch.empty(nc, **i32),
+                   child=torch.empty(nc, **i32), parent=torch.empty(nc, **i32),
+                   depth=torch.empty(nc, **i32), glo=torch.empty(nc, 3, **i32),
+                   ghi=torch.empty(nc, 3, **i32), abar=torch.empty(nc, **f32),
+                   dalpha=torch.empty(nc, **f32), lum=torch.empty(nc, **f32),
+                   cen=torch.empty(nc, 3, **f32), l2=torch.empty(nc, **f32),
+                   src_first=torch.empty(nc, **i32), src_count=torch.empty(nc, **i32),
+                   src_order=torch.empty(max(ns, 1), **i32))
+        order = ("key", "perm", "leaf_of", "first", "count", "child", "parent", "depth", "glo",
+                 "ghi", "abar", "dalpha", "lum", "cen", "l2", "src_first", "src_count",
+                 "src_order")
+        rc = self._lib.trevr_tree_export(self._h, *(ctypes.c_void_p(out[k].data_ptr())
+                                                     for k in order), _stream_ptr(stream))
+        if rc != TREVR_OK:
+            raise TrevrError(rc, "trevr_tree_export")
+        out["src_order"] = out["src_order"][:ns]
+        return out
+
+
+def build_tree(gas_xyz, alpha, src_xyz, src_lum, weight=None, lo=(0.0, 0.0, 0.0), side=1.0,
+               bucket=8, stream=None) -> Tree:
+    return Tree(gas_xyz, alpha, src_xyz, src_lum, weight, lo, side, bucket, stream)
+
+
+def compute_flux(tree: Tree, theta=0.75, tau_ref=0.1, sink_idx=None, out=None, counters=False,
+                 stats=False, stream=None, **tuning):
+    """Flux at the sinks (trevr_compute_flux). Returns flux, plus the per-sink counters
+    (n, 4) int32 and/or a stats dict when asked."""
+    lib = tree._lib
+    n = tree.n_gas if sink_idx is None else int(sink_idx.shape[0])
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=tree.device)
+    elif out.numel() != n:
+        raise ValueError(f"out has {out.numel()} elements, expected {n}")
+    cnt = torch.empty(n, 4, dtype=torch.int32, device=tree.device) if counters else None
+    st = Stats() if stats else None
+    prm = make_params(theta, tau_ref, tree.bucket, **tuning)
+    rc = lib.trevr_compute_flux(tree.handle, _dev_ptr(sink_idx, torch.int64, "sink_idx"), n,
+                                ctypes.byref(prm), _dev_ptr(out, torch.float32, "out"),
+                                _dev_ptr(cnt, torch.int32, "counters"),
+                                ctypes.byref(st) if st is not None else None, _stream_ptr(stream))
+    if rc != TREVR_OK:
+        raise TrevrError(rc, "trevr_compute_flux")
+    res = [out]
+    if counters:
+        res.append(cnt)
+    if stats:
+        res.append(st.as_dict())
+    return res[0] if len(res) == 1 else tuple(res)
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libtrevr so far in this process."""
+    return int(load_library().trevr_kernel_launches())
+
+
+def check(tree: Tree, stream=None):
+    rc = tree._lib.trevr_check(tree.handle, _stream_ptr(stream))
+    if rc != TREVR_OK:
+        raise TrevrError(rc, "trevr_check")
