@@ -336,6 +336,29 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_profile(args):
+    """A short program for ncu: one tree build, then the walk twice on a seeded sample
+    of sinks (the second launch is the one to capture)."""
+    import torch
+    from paper_1902_08083_gb300 import trevr
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    P, desc = _problem(args.workload)
+    n = int(P["gas_xyz"].shape[1])
+    g = {k: torch.from_numpy(np.ascontiguousarray(P[k])).to(dev)
+         for k in ("gas_xyz", "alpha", "src_xyz", "src_lum")}
+    tree = trevr.build_tree(g["gas_xyz"], g["alpha"], g["src_xyz"], g["src_lum"], lo=P["lo"],
+                            side=P["side"], bucket=P["bucket"])
+    m = min(n, args.sink_sample) if args.sink_sample > 0 else n
+    sinks = torch.from_numpy(workloads.sink_sample(n, m, seed=11)).to(dev)
+    for _ in range(2):
+        f = trevr.compute_flux(tree, P["theta"], P["tau_ref"], sink_idx=sinks)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.workload, "n_gas": n, "sinks": m,
+                      "flux_sum": float(f.double().sum())}), flush=True)
+    tree.free()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -346,10 +369,15 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=2048)
     ap.add_argument("--ref-sample", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="build once and run the walk twice on --sink-sample sinks (for ncu)")
+    ap.add_argument("--sink-sample", type=int, default=1 << 18)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -11,6 +11,7 @@
 #include <cstring>
 #include <vector>
 
+#include "morton.cuh"
 #include "primitives.cuh"
 #include "trevr_internal.cuh"
 
@@ -19,45 +20,6 @@ namespace trevr {
 // ------------------------------------------------------------------------------------
 // Morton keys
 // ------------------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long expand3(unsigned v) {
-  unsigned long long x = v & 0x1fffffull;
-  x = (x | (x << 32)) & 0x1f00000000ffffull;
-  x = (x | (x << 16)) & 0x1f0000ff0000ffull;
-  x = (x | (x << 8)) & 0x100f00f00f00f00full;
-  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
-  x = (x | (x << 2)) & 0x1249249249249249ull;
-  return x;
-}
-
-__device__ __forceinline__ unsigned compact3(unsigned long long x) {
-  x &= 0x1249249249249249ull;
-  x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
-  x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
-  x = (x ^ (x >> 8)) & 0x1f0000ff0000ffull;
-  x = (x ^ (x >> 16)) & 0x1f00000000ffffull;
-  x = (x ^ (x >> 32)) & 0x1fffffull;
-  return (unsigned)x;
-}
-
-// grid coordinate of key along axis a (0 = x, the most significant)
-__device__ __forceinline__ unsigned key_coord(unsigned long long key, int a) {
-  return compact3(key >> (2 - a));
-}
-
-struct Domain32 {
-  float lo[3], hi[3], scale, h;
-};
-
-// q = floor((x - lo) * scale) in fp32 (one rounded subtraction, one rounded
-// multiplication), clamped to 2^21 - 1. Caller has checked lo <= x < hi.
-__device__ __forceinline__ unsigned quantize(float x, float lo, float scale) {
-  float t = __fmul_rn(__fsub_rn(x, lo), scale);
-  unsigned q = __float2uint_rz(t);
-  return q > (unsigned)(kGridMax - 1) ? (unsigned)(kGridMax - 1) : q;
-}
-
-__device__ __forceinline__ bool in_dom(float x, float lo, float hi) { return x >= lo && x < hi; }
-
 __global__ void keys_kernel(const float* __restrict__ xyz, const float* __restrict__ alpha,
                             const float* __restrict__ weight, int n, Domain32 D,
                             unsigned long long* __restrict__ keys, unsigned* __restrict__ vals,
@@ -115,10 +77,10 @@ __global__ void scan_add_kernel(unsigned* data, int n, const unsigned* tile_offs
     if (base + j < n) data[base + j] += o;
 }
 
-static int scan_tiles(int n) { return (n + kScanTile - 1) / kScanTile; }
+int scan_tiles(int n) { return (n + kScanTile - 1) / kScanTile; }
 
 // scratch must hold scan_scratch_words(n) unsigned
-static size_t scan_scratch_words(int n) {
+size_t scan_scratch_words(int n) {
   size_t w = 0;
   while (n > 1) {
     n = scan_tiles(n);
@@ -199,20 +161,13 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
   }
 }
 
-struct SortScratch {
-  unsigned long long* k2;
-  unsigned* v2;
-  unsigned* counts;
-  unsigned* scan_scratch;
-};
-
-static size_t sort_count_words(int n) {
+size_t sort_count_words(int n) {
   int tiles = (n + kSortTile - 1) / kSortTile;
   return (size_t)256 * (size_t)(tiles > 0 ? tiles : 1);
 }
 
 // Sorts (k, v) by bits [0, bits) of k; result ends in (k, v). Uses the scratch buffers.
-static void radix_sort(unsigned long long* k, unsigned* v, int n, int bits, const SortScratch& S,
+void radix_sort(unsigned long long* k, unsigned* v, int n, int bits, const SortScratch& S,
                        cudaStream_t s) {
   if (n <= 1) return;
   const int tiles = (n + kSortTile - 1) / kSortTile;

@@ -95,6 +95,20 @@ int build_tree_impl(const float* gas_xyz, const float* alpha, const float* weigh
                     const trevr_domain* dom, int bucket, cudaStream_t s, trevr_tree** out,
                     float* build_ms);
 
+// ---- build.cu: stable LSD radix sort of (uint64 key, uint32 value) pairs
+struct SortScratch {
+  unsigned long long* k2;  // n keys
+  unsigned* v2;            // n values
+  unsigned* counts;        // sort_count_words(n)
+  unsigned* scan_scratch;  // scan_scratch_words(sort_count_words(n))
+};
+size_t sort_count_words(int n);
+size_t scan_scratch_words(int n);
+int scan_tiles(int n);
+// sorts (k, v) in place by bits [0, bits) of k
+void radix_sort(unsigned long long* k, unsigned* v, int n, int bits, const SortScratch& S,
+                cudaStream_t s);
+
 // ---- walk.cu
 struct WalkParams {
   float theta2;  // theta_open^2 (fp32)
