@@ -77,6 +77,14 @@ def _load():
         lib.orc_sink_interactions.restype = i64
         lib.orc_ray_tau.argtypes = [P, i64, i64, P, f32, P, P]
         lib.orc_ray_tau.restype = ctypes.c_double
+        lib.orc_adjoint.argtypes = [P, P, i64, P, f32, f32, P, P, ctypes.c_int]
+        lib.orc_adjoint.restype = ctypes.c_int
+        lib.orc_replay_record.argtypes = [P, P, i64, f32, f32, ctypes.POINTER(P)]
+        lib.orc_replay_record.restype = ctypes.c_int
+        lib.orc_replay_free.argtypes = [P]
+        lib.orc_replay_free.restype = None
+        lib.orc_replay_loss.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_double]
+        lib.orc_replay_loss.restype = ctypes.c_double
         lib.orc_leaf_of_point.argtypes = [P, f32, f32, f32]
         lib.orc_leaf_of_point.restype = i64
         _lib = lib
@@ -238,5 +246,53 @@ class OracleTree:
                                   ctypes.byref(ls), ctypes.byref(ns))
         return t, ls.value, ns.value
 
+    def adjoint(self, theta, tau_ref, grad_flux, sinks=None, nthreads=0):
+        """FP64 gradients (grad_lum[n_src], grad_alpha[n_gas], caller order) of a loss with
+        dLoss/dF = grad_flux at the sinks, decisions frozen."""
+        if sinks is None:
+            sinks = np.arange(self.n_gas, dtype=np.int64)
+        sinks = np.ascontiguousarray(sinks, dtype=np.int64)
+        g = np.ascontiguousarray(grad_flux, dtype=np.float64)
+        gl = np.zeros(self.n_src)
+        ga = np.zeros(self.n_gas)
+        rc = self._lib.orc_adjoint(self._h, _ptr(sinks), len(sinks), _ptr(g), float(theta),
+                                   float(tau_ref), _ptr(gl), _ptr(ga), int(nthreads))
+        if rc != ORC_OK:
+            raise OracleError(rc)
+        return gl, ga
+
+    def replay(self, theta, tau_ref, sinks=None):
+        """Record the decisions of the forward pass for `sinks`; returns a Replay."""
+        if sinks is None:
+            sinks = np.arange(self.n_gas, dtype=np.int64)
+        sinks = np.ascontiguousarray(sinks, dtype=np.int64)
+        h = ctypes.c_void_p()
+        rc = self._lib.orc_replay_record(self._h, _ptr(sinks), len(sinks), float(theta),
+                                         float(tau_ref), ctypes.byref(h))
+        if rc != ORC_OK:
+            raise OracleError(rc)
+        return Replay(self, h, len(sinks))
+
     def leaf_of_point(self, x, y, z):
         return int(self._lib.orc_leaf_of_point(self._h, float(x), float(y), float(z)))
+
+
+class Replay:
+    """Frozen decisions of one forward pass; evaluates sum_k w_k log F_k under a single
+    perturbed luminosity (kind 0) or absorption coefficient (kind 1)."""
+
+    def __init__(self, tree, handle, n_sink):
+        self.tree = tree
+        self._h = handle
+        self.n_sink = n_sink
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self.tree._lib.orc_replay_free(self._h)
+            self._h = None
+
+    def loss(self, w, kind=-1, index=0, h=0.0):
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        assert w.shape[0] == self.n_sink
+        return float(self.tree._lib.orc_replay_loss(self.tree._h, self._h, _ptr(w), int(kind),
+                                                    int(index), float(h)))

@@ -945,3 +945,471 @@ int64_t orc_leaf_of_point(const orc_tree *T, float x, float y, float z)
                      quantize32(z, T->lo32[2], scale)};
     return leaf_of_point(T, g);
 }
+
+/* ======================================================================== */
+/* Adjoint with frozen decisions (differentiation of Eq. simpint).          */
+/*                                                                          */
+/* For a loss with dLoss/dF_p = g_p, every interaction (p, C) contributes   */
+/* f = L_C exp(-tau) / (4 pi s^2), s = |q - p|, tau = sum_X abar_X l_X(q).  */
+/* The accept / refine / touch decisions are held fixed; the centre of      */
+/* luminosity q = c_C = sum_j L_j y_j / L_C moves with the luminosities.    */
+/*   df/dL_C = f / L_C ;  dc_C/dL_j = (y_j - c_C) / L_C   (j in C)          */
+/*   grad_q f = f (-2 (q - p)/s^2 - sum_X abar_X grad_q l_X)                */
+/*   df/dabar_X = -f l_X ;  dabar_X/dalpha_i = w_i / W_X    (i in X)        */
+/* l_X = (t_exit - t_enter) |q - p|, with t of a slab plane b on axis k     */
+/* equal to (b - p_k)/(q_k - p_k), so dt/dq_k = -t/(q_k - p_k); a t clamped */
+/* to 0 or 1 (the ray starts or ends inside X) does not move.               */
+/* ======================================================================== */
+
+typedef struct {
+    double *a;     /* per node: sum g f / L_C over merged interactions with C */
+    double *b;     /* per node, 3: sum g grad_q f / L_C */
+    double *e;     /* per sorted source: sum g f / L_j over single-source interactions */
+    double *G;     /* per node: sum -g f l_X over segments using X */
+} adj_acc_t;
+
+/* FP64 length and its gradient w.r.t. the ray's end point q. */
+static double clip64_grad(const orc_tree *T, const ray_t *R, int64_t X, double grad[3])
+{
+    double t0 = 0.0, t1 = 1.0;
+    int k0 = -1, k1 = -1;
+    for (int k = 0; k < 3; ++k) {
+        double lo = T->lo[k] + (double)T->glo[X][k] * T->h;
+        double hi = T->lo[k] + (double)T->ghi[X][k] * T->h;
+        if (R->D[k] != 0.0) {
+            double ta = (lo - R->P[k]) / R->D[k];
+            double tb = (hi - R->P[k]) / R->D[k];
+            double tn = fmin(ta, tb), tx = fmax(ta, tb);
+            if (tn > t0) { t0 = tn; k0 = k; }
+            if (tx < t1) { t1 = tx; k1 = k; }
+        } else if (R->P[k] < lo || R->P[k] > hi) {
+            grad[0] = grad[1] = grad[2] = 0.0;
+            return 0.0;
+        }
+    }
+    if (!(t1 > t0)) {
+        grad[0] = grad[1] = grad[2] = 0.0;
+        return 0.0;
+    }
+    double dt[3] = {0.0, 0.0, 0.0};
+    if (k1 >= 0) dt[k1] += -t1 / R->D[k1];
+    if (k0 >= 0) dt[k0] -= -t0 / R->D[k0];
+    for (int k = 0; k < 3; ++k) grad[k] = dt[k] * R->LEN + (t1 - t0) * R->D[k] / R->LEN;
+    return (t1 - t0) * R->LEN;
+}
+
+typedef struct {
+    int64_t *box;
+    double *len;
+    int64_t n, cap;
+} seglist_t;
+
+static void seglist_push(seglist_t *s, int64_t X, double l)
+{
+    if (s->n == s->cap) {
+        int64_t nc = s->cap ? 2 * s->cap : 64;
+        s->box = realloc(s->box, (size_t)nc * sizeof(int64_t));
+        s->len = realloc(s->len, (size_t)nc * sizeof(double));
+        s->cap = nc;
+    }
+    s->box[s->n] = X;
+    s->len[s->n] = l;
+    s->n++;
+}
+
+/* the unrefined segments of a ray, with the same decisions as seg() */
+static void seg_list(const orc_tree *T, const ray_t *R, int64_t X, float tau_ref, seglist_t *out)
+{
+    float l32 = clip32(R, T->blo32[X], T->bhi32[X]);
+    if (!(l32 > 0.0f)) return;
+    if (T->split_bit[X] >= 0 && ((tau_ref <= 0.0f) || (T->dalpha32[X] * l32 > tau_ref))) {
+        seg_list(T, R, T->lower[X], tau_ref, out);
+        seg_list(T, R, T->upper[X], tau_ref, out);
+        return;
+    }
+    seglist_push(out, X, 0.0);
+}
+
+static void ray_segments(const orc_tree *T, const ray_t *R, int64_t S, int64_t C, float tau_ref,
+                         seglist_t *out)
+{
+    seg_list(T, R, S, tau_ref, out);
+    if (S == C) return;
+    seg_list(T, R, C, tau_ref, out);
+    int64_t u = S, v = C;
+    while (T->depth[u] > T->depth[v]) {
+        seg_list(T, R, sibling_of(T, u), tau_ref, out);
+        u = T->parent[u];
+    }
+    while (T->depth[v] > T->depth[u]) {
+        seg_list(T, R, sibling_of(T, v), tau_ref, out);
+        v = T->parent[v];
+    }
+    while (T->parent[u] != T->parent[v]) {
+        seg_list(T, R, sibling_of(T, u), tau_ref, out);
+        seg_list(T, R, sibling_of(T, v), tau_ref, out);
+        u = T->parent[u];
+        v = T->parent[v];
+    }
+}
+
+static void make_ray(const orc_tree *T, int64_t i, const float q32[3], const double q64[3], ray_t *R)
+{
+    R->p[0] = T->px[i];
+    R->p[1] = T->py[i];
+    R->p[2] = T->pz[i];
+    for (int k = 0; k < 3; ++k) {
+        R->d[k] = q32[k] - R->p[k];
+        R->inv[k] = R->d[k] != 0.0f ? 1.0f / R->d[k] : 0.0f;
+        R->P[k] = (double)R->p[k];
+        R->D[k] = q64[k] - R->P[k];
+    }
+    R->len = sqrtf(R->d[0] * R->d[0] + R->d[1] * R->d[1] + R->d[2] * R->d[2]);
+    R->LEN = sqrt(R->D[0] * R->D[0] + R->D[1] * R->D[1] + R->D[2] * R->D[2]);
+}
+
+#define ATOMIC_ADD(ptr, v) \
+    do { \
+        double _v = (v); \
+        _Pragma("omp atomic") *(ptr) += _v; \
+    } while (0)
+
+/* one interaction of the adjoint: accumulate into acc */
+static void adj_interaction(const orc_tree *T, int64_t i, int64_t S, int64_t C, const float q32[3],
+                            const double q64[3], double L, float tau_ref, float smin2, double g,
+                            int64_t src, adj_acc_t *acc)
+{
+    ray_t R;
+    make_ray(T, i, q32, q64, &R);
+    float s2 = R.d[0] * R.d[0] + R.d[1] * R.d[1] + R.d[2] * R.d[2];
+    if (s2 < smin2) return;
+    seglist_t sl = {NULL, NULL, 0, 0};
+    ray_segments(T, &R, S, C, tau_ref, &sl);
+    nsum_t tau = {0.0, 0.0};
+    double gtau[3] = {0.0, 0.0, 0.0};
+    for (int64_t k = 0; k < sl.n; ++k) {
+        double gl[3];
+        double l = clip64_grad(T, &R, sl.box[k], gl);
+        sl.len[k] = l;
+        nsum_add(&tau, T->abar[sl.box[k]] * l);
+        for (int d = 0; d < 3; ++d) gtau[d] += T->abar[sl.box[k]] * gl[d];
+    }
+    double S2 = R.D[0] * R.D[0] + R.D[1] * R.D[1] + R.D[2] * R.D[2];
+    double f = L * exp(-nsum_get(&tau)) / (4.0 * M_PI * S2);
+    for (int64_t k = 0; k < sl.n; ++k) ATOMIC_ADD(&acc->G[sl.box[k]], -g * f * sl.len[k]);
+    if (src >= 0) {
+        ATOMIC_ADD(&acc->e[src], g * f / L);
+    } else {
+        ATOMIC_ADD(&acc->a[C], g * f / L);
+        for (int d = 0; d < 3; ++d) {
+            double gq = f * (-2.0 * R.D[d] / S2 - gtau[d]);
+            ATOMIC_ADD(&acc->b[3 * C + d], g * gq / L);
+        }
+    }
+    free(sl.box);
+    free(sl.len);
+}
+
+static void adj_sink(const orc_tree *T, int64_t i, float theta, float tau_ref, double g,
+                     adj_acc_t *acc)
+{
+    const float theta2 = theta * theta;
+    const float smin = 1e-12f * T->side32;
+    const float smin2 = smin * smin;
+    const float p[3] = {T->px[i], T->py[i], T->pz[i]};
+    const int64_t S = T->leaf_of[i];
+    int64_t stack[MAXDEPTH + 2];
+    int sp = 0;
+    stack[sp++] = ROOT;
+    while (sp > 0) {
+        int64_t X = stack[--sp];
+        if (!(T->L[X] > 0.0)) continue;
+        float r2 = 0.0f;
+        for (int d = 0; d < 3; ++d) {
+            float e = fmaxf(fmaxf(T->blo32[X][d] - p[d], p[d] - T->bhi32[X][d]), 0.0f);
+            r2 = r2 + e * e;
+        }
+        if (T->l2_32[X] < theta2 * r2) {
+            adj_interaction(T, i, S, X, T->cen32[X], T->cen[X], T->L[X], tau_ref, smin2, g, -1,
+                            acc);
+        } else if (T->split_bit[X] < 0) {
+            for (int64_t s = T->src_first[X]; s < T->src_first[X] + T->src_count[X]; ++s) {
+                if (!(T->slum[s] > 0.0f)) continue;
+                const float q32[3] = {T->sx[s], T->sy[s], T->sz[s]};
+                const double q64[3] = {(double)T->sx[s], (double)T->sy[s], (double)T->sz[s]};
+                adj_interaction(T, i, S, X, q32, q64, (double)T->slum[s], tau_ref, smin2, g, s,
+                                acc);
+            }
+        } else {
+            stack[sp++] = T->upper[X];
+            stack[sp++] = T->lower[X];
+        }
+    }
+}
+
+/*
+ * Gradients of a loss with dLoss/dF = grad_flux (one entry per sink in
+ * `sinks`, caller indices) with respect to the source luminosities
+ * (grad_lum, n_src, caller order) and the particle absorption coefficients
+ * (grad_alpha, n_gas, caller order). Decisions frozen (see above).
+ */
+int orc_adjoint(const orc_tree *T, const int64_t *sinks, int64_t n_sink, const double *grad_flux,
+                float theta, float tau_ref, double *grad_lum, double *grad_alpha, int nthreads)
+{
+    for (int64_t k = 0; k < n_sink; ++k)
+        if (sinks[k] < 0 || sinks[k] >= T->n_gas) return ORC_ERR_INVALID_ARGUMENT;
+    const int64_t nn = T->n_nodes;
+    adj_acc_t acc;
+    acc.a = calloc((size_t)nn, sizeof(double));
+    acc.b = calloc((size_t)(3 * nn), sizeof(double));
+    acc.e = calloc((size_t)(T->n_src > 0 ? T->n_src : 1), sizeof(double));
+    acc.G = calloc((size_t)nn, sizeof(double));
+    if (!acc.a || !acc.b || !acc.e || !acc.G) {
+        free(acc.a);
+        free(acc.b);
+        free(acc.e);
+        free(acc.G);
+        return ORC_ERR_NO_MEMORY;
+    }
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t k = 0; k < n_sink; ++k)
+        if (grad_flux[k] != 0.0) adj_sink(T, T->rank[sinks[k]], theta, tau_ref, grad_flux[k], &acc);
+
+    /* luminosities: single-source terms plus, for every ancestor C of the
+       source's leaf (the leaf included), a_C + b_C . (y_j - c_C) */
+    for (int64_t s = 0; s < T->n_src; ++s) {
+        double gsum = acc.e[s];
+        const double y[3] = {(double)T->sx[s], (double)T->sy[s], (double)T->sz[s]};
+        for (int64_t C = T->src_leaf[s]; C >= 0; C = T->parent[C]) {
+            gsum += acc.a[C];
+            for (int d = 0; d < 3; ++d) gsum += acc.b[3 * C + d] * (y[d] - T->cen[C][d]);
+        }
+        grad_lum[T->src_order[s]] = gsum;
+    }
+    /* absorption: w_i sum over the cells X holding i of G_X / W_X */
+    for (int64_t i = 0; i < T->n_gas; ++i) {
+        double gsum = 0.0;
+        for (int64_t X = T->leaf_of[i]; X >= 0; X = T->parent[X]) gsum += acc.G[X] / T->W[X];
+        grad_alpha[T->perm[i]] = (double)T->w[i] * gsum;
+    }
+    free(acc.a);
+    free(acc.b);
+    free(acc.e);
+    free(acc.G);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Replay: the loss sum_p w_p log F_p re-evaluated with the decisions of the */
+/* unperturbed forward pass (interactions and segment cells recorded), for   */
+/* one perturbed input. Used for central finite differences of the adjoint.  */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t n_sink;
+    int64_t *sink_i;     /* sorted particle index of each sink */
+    int64_t *ia_start;   /* n_sink+1: range of interactions */
+    int64_t *ia_node;    /* C */
+    int64_t *ia_src;     /* sorted source index or -1 */
+    int64_t *ia_seg0;    /* n_ia+1: range of segment cells */
+    int64_t *seg_box;
+    int64_t n_ia, n_seg;
+} orc_replay;
+
+void orc_replay_free(orc_replay *r)
+{
+    if (!r) return;
+    free(r->sink_i);
+    free(r->ia_start);
+    free(r->ia_node);
+    free(r->ia_src);
+    free(r->ia_seg0);
+    free(r->seg_box);
+    free(r);
+}
+
+typedef struct {
+    int64_t *node, *src, *nseg;
+    int64_t n, cap;
+    seglist_t segs;
+} rec_buf_t;
+
+static void rec_interaction(const orc_tree *T, int64_t i, int64_t S, int64_t C, const float q32[3],
+                            const double q64[3], float tau_ref, float smin2, int64_t src,
+                            rec_buf_t *rb)
+{
+    ray_t R;
+    make_ray(T, i, q32, q64, &R);
+    float s2 = R.d[0] * R.d[0] + R.d[1] * R.d[1] + R.d[2] * R.d[2];
+    if (s2 < smin2) return;
+    int64_t before = rb->segs.n;
+    ray_segments(T, &R, S, C, tau_ref, &rb->segs);
+    if (rb->n == rb->cap) {
+        int64_t nc = rb->cap ? 2 * rb->cap : 64;
+        rb->node = realloc(rb->node, (size_t)nc * sizeof(int64_t));
+        rb->src = realloc(rb->src, (size_t)nc * sizeof(int64_t));
+        rb->nseg = realloc(rb->nseg, (size_t)nc * sizeof(int64_t));
+        rb->cap = nc;
+    }
+    rb->node[rb->n] = C;
+    rb->src[rb->n] = src;
+    rb->nseg[rb->n] = rb->segs.n - before;
+    rb->n++;
+}
+
+int orc_replay_record(const orc_tree *T, const int64_t *sinks, int64_t n_sink, float theta,
+                      float tau_ref, orc_replay **out)
+{
+    *out = NULL;
+    orc_replay *r = calloc(1, sizeof(orc_replay));
+    rec_buf_t rb;
+    memset(&rb, 0, sizeof(rb));
+    r->n_sink = n_sink;
+    r->sink_i = malloc((size_t)(n_sink + 1) * sizeof(int64_t));
+    r->ia_start = malloc((size_t)(n_sink + 1) * sizeof(int64_t));
+    const float theta2 = theta * theta;
+    const float smin = 1e-12f * T->side32;
+    const float smin2 = smin * smin;
+    for (int64_t k = 0; k < n_sink; ++k) {
+        int64_t i = T->rank[sinks[k]];
+        r->sink_i[k] = i;
+        r->ia_start[k] = rb.n;
+        const float p[3] = {T->px[i], T->py[i], T->pz[i]};
+        const int64_t S = T->leaf_of[i];
+        int64_t stack[MAXDEPTH + 2];
+        int sp = 0;
+        stack[sp++] = ROOT;
+        while (sp > 0) {
+            int64_t X = stack[--sp];
+            if (!(T->L[X] > 0.0)) continue;
+            float r2 = 0.0f;
+            for (int d = 0; d < 3; ++d) {
+                float e = fmaxf(fmaxf(T->blo32[X][d] - p[d], p[d] - T->bhi32[X][d]), 0.0f);
+                r2 = r2 + e * e;
+            }
+            if (T->l2_32[X] < theta2 * r2) {
+                rec_interaction(T, i, S, X, T->cen32[X], T->cen[X], tau_ref, smin2, -1, &rb);
+            } else if (T->split_bit[X] < 0) {
+                for (int64_t s = T->src_first[X]; s < T->src_first[X] + T->src_count[X]; ++s) {
+                    if (!(T->slum[s] > 0.0f)) continue;
+                    const float q32[3] = {T->sx[s], T->sy[s], T->sz[s]};
+                    const double q64[3] = {(double)T->sx[s], (double)T->sy[s], (double)T->sz[s]};
+                    rec_interaction(T, i, S, X, q32, q64, tau_ref, smin2, s, &rb);
+                }
+            } else {
+                stack[sp++] = T->upper[X];
+                stack[sp++] = T->lower[X];
+            }
+        }
+    }
+    r->ia_start[n_sink] = rb.n;
+    r->n_ia = rb.n;
+    r->n_seg = rb.segs.n;
+    r->ia_node = rb.node;
+    r->ia_src = rb.src;
+    r->seg_box = rb.segs.box;
+    free(rb.segs.len);
+    r->ia_seg0 = malloc((size_t)(rb.n + 1) * sizeof(int64_t));
+    int64_t acc = 0;
+    for (int64_t q = 0; q < rb.n; ++q) {
+        r->ia_seg0[q] = acc;
+        acc += rb.nseg[q];
+    }
+    r->ia_seg0[rb.n] = acc;
+    free(rb.nseg);
+    *out = r;
+    return ORC_OK;
+}
+
+/* FP64 length of the segment p->q inside node X (no decisions). */
+static double seg_len64(const orc_tree *T, const double P[3], const double Q[3], int64_t X)
+{
+    double D[3] = {Q[0] - P[0], Q[1] - P[1], Q[2] - P[2]};
+    double t0 = 0.0, t1 = 1.0;
+    for (int k = 0; k < 3; ++k) {
+        double lo = T->lo[k] + (double)T->glo[X][k] * T->h;
+        double hi = T->lo[k] + (double)T->ghi[X][k] * T->h;
+        if (D[k] != 0.0) {
+            double ta = (lo - P[k]) / D[k], tb = (hi - P[k]) / D[k];
+            t0 = fmax(t0, fmin(ta, tb));
+            t1 = fmin(t1, fmax(ta, tb));
+        } else if (P[k] < lo || P[k] > hi) {
+            return 0.0;
+        }
+    }
+    return t1 > t0 ? (t1 - t0) * sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]) : 0.0;
+}
+
+/*
+ * Loss sum_k w[k] log F_k over the recorded sinks, with one input perturbed:
+ * kind 0: luminosity of source `index` (caller order) += h;
+ * kind 1: alpha of particle `index` (caller order) += h;
+ * kind -1: no perturbation.  Moments are updated exactly for the perturbation.
+ */
+double orc_replay_loss(const orc_tree *T, const orc_replay *r, const double *w, int kind,
+                       int64_t index, double h)
+{
+    /* perturbed quantities, as overrides of the affected nodes */
+    const int64_t nn = T->n_nodes;
+    double *dabar = calloc((size_t)nn, sizeof(double));
+    double *Lp = malloc((size_t)nn * sizeof(double));
+    double (*cp)[3] = malloc((size_t)nn * sizeof(*cp));
+    for (int64_t X = 0; X < nn; ++X) {
+        Lp[X] = T->L[X];
+        for (int d = 0; d < 3; ++d) cp[X][d] = T->cen[X][d];
+    }
+    int64_t psrc = -1;
+    double srcL = 0.0;
+    if (kind == 0) {
+        for (int64_t s = 0; s < T->n_src; ++s)
+            if (T->src_order[s] == index) psrc = s;
+        const double y[3] = {(double)T->sx[psrc], (double)T->sy[psrc], (double)T->sz[psrc]};
+        for (int64_t C = T->src_leaf[psrc]; C >= 0; C = T->parent[C]) {
+            double Ln = T->L[C] + h;
+            for (int d = 0; d < 3; ++d) cp[C][d] = (T->L[C] * T->cen[C][d] + h * y[d]) / Ln;
+            Lp[C] = Ln;
+        }
+        srcL = (double)T->slum[psrc] + h;
+    } else if (kind == 1) {
+        int64_t i = T->rank[index];
+        for (int64_t X = T->leaf_of[i]; X >= 0; X = T->parent[X])
+            dabar[X] = (double)T->w[i] * h / T->W[X];
+    }
+    double loss = 0.0;
+#ifdef _OPENMP
+#pragma omp parallel for reduction(+ : loss) schedule(dynamic, 16)
+#endif
+    for (int64_t k = 0; k < r->n_sink; ++k) {
+        int64_t i = r->sink_i[k];
+        const double P[3] = {(double)T->px[i], (double)T->py[i], (double)T->pz[i]};
+        nsum_t F = {0.0, 0.0};
+        for (int64_t q = r->ia_start[k]; q < r->ia_start[k + 1]; ++q) {
+            int64_t C = r->ia_node[q], s = r->ia_src[q];
+            double Q[3], L;
+            if (s >= 0) {
+                Q[0] = (double)T->sx[s];
+                Q[1] = (double)T->sy[s];
+                Q[2] = (double)T->sz[s];
+                L = (s == psrc) ? srcL : (double)T->slum[s];
+            } else {
+                for (int d = 0; d < 3; ++d) Q[d] = cp[C][d];
+                L = Lp[C];
+            }
+            nsum_t tau = {0.0, 0.0};
+            for (int64_t g = r->ia_seg0[q]; g < r->ia_seg0[q + 1]; ++g) {
+                int64_t X = r->seg_box[g];
+                nsum_add(&tau, (T->abar[X] + dabar[X]) * seg_len64(T, P, Q, X));
+            }
+            double s2 = 0.0;
+            for (int d = 0; d < 3; ++d) s2 += (Q[d] - P[d]) * (Q[d] - P[d]);
+            nsum_add(&F, L * exp(-nsum_get(&tau)) / (4.0 * M_PI * s2));
+        }
+        loss += w[k] * log(nsum_get(&F));
+    }
+    free(dabar);
+    free(Lp);
+    free(cp);
+    return loss;
+}
