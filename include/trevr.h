@@ -161,6 +161,37 @@ int trevr_tree_export(const trevr_tree* t, unsigned long long* key, int* perm, i
 /* Release the tree and every buffer it holds (synchronises the device). */
 void trevr_tree_free(trevr_tree* t);
 
+/*
+ * Morton keys and stable sort of the gas particles WITHOUT any device
+ * allocation. The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory while they run -- a host code
+ * that reserves its device memory up front and forbids allocation inside its
+ * time-step loop, or a plug-in that only receives buffers from the application
+ * that owns the GPU. Its scratch memory is a fixed file-scope device array
+ * sized for TREVR_NOALLOC_MAX_N particles (about 12.3 MiB, held on every GPU
+ * that loads the library until the process exits).
+ *
+ * The result is the same as the keys and the permutation of trevr_build_tree
+ * (see trevr_tree_export): Morton keys with 21 bits per axis, x most
+ * significant, computed in fp32 from the domain, sorted stably.
+ *
+ *   gas_xyz   3*n_gas floats (SoA), device.
+ *   n_gas     1 .. TREVR_NOALLOC_MAX_N; larger sizes return
+ *             TREVR_ERR_INVALID_ARGUMENT without touching the GPU.
+ *   dom       host pointer to the domain.
+ *   keys_out  n_gas uint64, device: the keys in sorted order.
+ *   perm_out  n_gas int32, device: caller index of the i-th sorted particle.
+ *   stream    cudaStream_t. The call synchronises it before returning.
+ * The first call on a device looks up the device address of the scratch array
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture. Every call shares the one array and overwrites it, so
+ * calls whose work overlaps on the GPU (other streams or host threads) race.
+ * A point outside the domain returns TREVR_ERR_OUT_OF_DOMAIN.
+ */
+#define TREVR_NOALLOC_MAX_N (1 << 20)
+int trevr_morton_sort_noalloc(const float* gas_xyz, long long n_gas, const trevr_domain* dom,
+                              unsigned long long* keys_out, int* perm_out, void* stream);
+
 /* Number of CUDA kernels this library has launched in the calling process
    (all devices, all streams); for launch accounting in benchmarks. */
 unsigned long long trevr_kernel_launches(void);

@@ -30,7 +30,9 @@ ERRORS = {
 EXPORTS = (
     "trevr_build_tree", "trevr_compute_flux", "trevr_check", "trevr_tree_info",
     "trevr_tree_export", "trevr_tree_free", "trevr_status_string", "trevr_kernel_launches",
+    "trevr_morton_sort_noalloc",
 )
+NOALLOC_MAX_N = 1 << 20
 
 
 class TrevrError(RuntimeError):
@@ -91,6 +93,8 @@ def load_library(path: str = LIB_PATH):
         lib.trevr_tree_export.restype = ctypes.c_int
         lib.trevr_tree_free.argtypes = [P]
         lib.trevr_tree_free.restype = None
+        lib.trevr_morton_sort_noalloc.argtypes = [P, ll, ctypes.POINTER(Domain), P, P, P]
+        lib.trevr_morton_sort_noalloc.restype = ctypes.c_int
         lib.trevr_kernel_launches.argtypes = []
         lib.trevr_kernel_launches.restype = ctypes.c_ulonglong
         lib.trevr_status_string.argtypes = [ctypes.c_int]
@@ -231,6 +235,27 @@ def compute_flux(tree: Tree, theta=0.75, tau_ref=0.1, sink_idx=None, out=None, c
     if stats:
         res.append(st.as_dict())
     return res[0] if len(res) == 1 else tuple(res)
+
+
+def morton_sort_noalloc(gas_xyz, lo=(0.0, 0.0, 0.0), side=1.0, keys_out=None, perm_out=None,
+                        stream=None):
+    """Morton keys and stable sort of the particles (trevr_morton_sort_noalloc): the
+    library allocates nothing; the output tensors are allocated here unless given."""
+    lib = load_library()
+    n = int(gas_xyz.shape[1])
+    if keys_out is None:
+        keys_out = torch.empty(n, dtype=torch.int64, device=gas_xyz.device)
+    if perm_out is None:
+        perm_out = torch.empty(n, dtype=torch.int32, device=gas_xyz.device)
+    dom = Domain((ctypes.c_float * 3)(*[float(v) for v in lo]), float(side))
+    rc = lib.trevr_morton_sort_noalloc(_dev_ptr(gas_xyz.contiguous(), torch.float32, "gas_xyz"),
+                                       n, ctypes.byref(dom),
+                                       _dev_ptr(keys_out, torch.int64, "keys_out"),
+                                       _dev_ptr(perm_out, torch.int32, "perm_out"),
+                                       _stream_ptr(stream))
+    if rc != TREVR_OK:
+        raise TrevrError(rc, "trevr_morton_sort_noalloc")
+    return keys_out, perm_out
 
 
 def kernel_launches() -> int:
