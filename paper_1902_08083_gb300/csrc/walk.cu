@@ -1,6 +1,6 @@
 // Sink walk, reverse ray and flux sum (Grond et al. 2019, Sec. 2.2.1-2.2.3).
 //
-// One thread per sink; sinks in Morton order, so the 32 sinks of a warp are
+// One lane per sink; sinks in Morton order, so the 32 sinks of a warp are
 // neighbours in space and walk almost the same cells. Per sink:
 //   * source walk: a cell with L > 0 is merged into one pseudo-source at its
 //     centre of luminosity when theta_open > l/r (Eq. openangle), tested as
@@ -8,18 +8,31 @@
 //     gives its sources one by one;
 //   * reverse ray to each pseudo-source: the segments are the sink's leaf S,
 //     the pseudo-source's cell C and the siblings of the cells on the two
-//     paths up to the children of their lowest common ancestor; each segment
+//     paths up to the children of their lowest common ancestor A; each segment
 //     uses the cell's mean absorption unless (alpha_max - alpha_min) * l >
 //     tau_ref (Eq. refcrit), in which case its children are used instead;
 //   * flux: sum of L exp(-tau) / (4 pi s^2) (Eq. simpint).
 // The decisions (opening angle, refinement, "does the ray touch the cell")
 // are evaluated with explicitly rounded fp32 operations in a fixed order.
+//
+// GPU form. Every lane runs one flat loop whose iterations are either one
+// walk step or one cell clip, so the lanes of a warp stay converged on the
+// clip work, which dominates (tens of clips per ray). The ancestors of the
+// sink's leaf are listed once per sink, and the walk keeps its depth-first
+// path, so the segment list of a ray is known without chasing parent links:
+// the sibling of a cell is its index XOR 1 (children are allocated in pairs),
+// and the common ancestor's depth is the length of the common prefix of the
+// two ancestor lists, kept as a bit mask during the walk.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "trevr_internal.cuh"
 
 namespace trevr {
+
+namespace {
+
+constexpr int kDepth = 64;  // > max cell depth (63): stacks and ancestor lists never overflow
 
 struct Ray {
   float px, py, pz;
@@ -70,104 +83,14 @@ struct CSum {
   __device__ __forceinline__ float get() const { return __fadd_rn(s, c); }
 };
 
-struct Counters {
-  int rays = 0, segs = 0, visited = 0, refines = 0, clips = 0;
-};
+}  // namespace
 
-template <int STACK>
-struct RayTracer {
-  const TreeView& T;
-  const WalkParams& P;
-  Ray R;
-  CSum tau;
-  Counters& cnt;
-  int* status;
-
-  __device__ RayTracer(const TreeView& t, const WalkParams& p, Counters& c, int* st)
-      : T(t), P(p), cnt(c), status(st) {}
-
-  // optical depth through cell X, refined where Eq. refcrit asks
-  __device__ __forceinline__ void seg(int X) {
-    int stack[STACK];
-    int sp = 0;
-    stack[sp++] = X;
-    while (sp > 0) {
-      const int Y = stack[--sp];
-      const float4 a = __ldg(&T.nA[Y]);
-      const float4 b = __ldg(&T.nB[Y]);
-      const float l = clip_len(R, a, b);
-      ++cnt.clips;
-      if (!(l > 0.0f)) continue;
-      const int child = __ldg(&T.nT[Y].x);
-      if (child >= 0 && (P.tau_ref <= 0.0f || __fmul_rn(b.w, l) > P.tau_ref)) {
-        if (sp + 2 > STACK) {
-          atomicOr(status, kStatusStackOverflow);
-          return;
-        }
-        ++cnt.refines;
-        stack[sp++] = child + 1;
-        stack[sp++] = child;
-        continue;
-      }
-      tau.add(a.w * l);
-      ++cnt.segs;
-    }
-  }
-
-  // flux of luminosity L at q (inside cell C) seen from the sink at p in leaf S
-  __device__ float contribute(float px, float py, float pz, int S, int C, float qx, float qy,
-                              float qz, float L) {
-    R.px = px;
-    R.py = py;
-    R.pz = pz;
-    R.dx = __fsub_rn(qx, px);
-    R.dy = __fsub_rn(qy, py);
-    R.dz = __fsub_rn(qz, pz);
-    const float s2 =
-        __fadd_rn(__fadd_rn(__fmul_rn(R.dx, R.dx), __fmul_rn(R.dy, R.dy)), __fmul_rn(R.dz, R.dz));
-    if (s2 < P.smin2) return 0.0f;  // a source on top of the sink adds nothing
-    R.len = __fsqrt_rn(s2);
-    R.ix = R.dx != 0.0f ? __frcp_rn(R.dx) : 0.0f;
-    R.iy = R.dy != 0.0f ? __frcp_rn(R.dy) : 0.0f;
-    R.iz = R.dz != 0.0f ? __frcp_rn(R.dz) : 0.0f;
-    tau = CSum();
-    seg(S);
-    if (S != C) {
-      seg(C);
-      int u = S, v = C;
-      int du = __ldg(&T.ndepth[u]), dv = __ldg(&T.ndepth[v]);
-      while (du > dv) {
-        seg(u ^ 1);
-        u = __ldg(&T.nT[u].y);
-        --du;
-      }
-      while (dv > du) {
-        seg(v ^ 1);
-        v = __ldg(&T.nT[v].y);
-        --dv;
-      }
-      while (true) {
-        const int pu = __ldg(&T.nT[u].y), pv = __ldg(&T.nT[v].y);
-        if (pu == pv) break;
-        seg(u ^ 1);
-        seg(v ^ 1);
-        u = pu;
-        v = pv;
-      }
-    }
-    ++cnt.rays;
-    const float t = tau.get();
-    return L * expf(-t) / (12.566370614359172f * s2);
-  }
-};
-
-template <int STACK>
-__global__ void __launch_bounds__(128) walk_plain_kernel(TreeView T, const long long* sink_idx,
-                                                         int n_sink, WalkParams P, float* flux_out,
-                                                         int* counters,
-                                                         unsigned long long* stats, int* status) {
+__global__ void __launch_bounds__(128) walk_flat_kernel(TreeView T, const long long* sink_idx,
+                                                        int n_sink, WalkParams P, float* flux_out,
+                                                        int* counters,
+                                                        unsigned long long* stats, int* status) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  Counters cnt;
+  int c_rays = 0, c_segs = 0, c_visit = 0, c_ref = 0, c_clip = 0;
   bool valid = k < n_sink;
   if (valid && sink_idx) {
     const long long si = sink_idx[k];
@@ -179,68 +102,189 @@ __global__ void __launch_bounds__(128) walk_plain_kernel(TreeView T, const long 
     }
   }
   if (valid) {
-    int i = sink_idx ? T.rank[sink_idx[k]] : k;
+    const int i = sink_idx ? T.rank[sink_idx[k]] : k;
     const float4 p = T.pos[i];
     const int S = T.leaf_of[i];
-    RayTracer<STACK> rt(T, P, cnt, status);
+    const int dS = __ldg(&T.ndepth[S]);
+    const int stack_limit = P.stack_depth < kDepth ? P.stack_depth : kDepth;
+
+    int anc[kDepth];     // ancestors of S by depth (anc[dS] = S)
+    int path[kDepth];    // current depth-first path of the walk
+    int wstack[kDepth];  // walk stack: cell index
+    int wdepth[kDepth];  //             and its depth
+    int rstack[kDepth];  // cells waiting to be clipped (refinement)
+    {
+      int u = S;
+      for (int d = dS; d >= 0; --d) {
+        anc[d] = u;
+        u = __ldg(&T.nT[u].y);
+      }
+    }
+    unsigned long long on_path = 0;  // bit d: path[d] is an ancestor of S (or S)
+    wstack[0] = kRoot;
+    wdepth[0] = 0;
+    int sp = 1;
+
     CSum F;
-    int stack[STACK];
-    int sp = 0;
-    stack[sp++] = kRoot;
-    const int limit = 2 * T.n_nodes_cap + 2;
-    int iters = 0;
-    while (sp > 0) {
-      const int X = stack[--sp];
-      if (++iters > limit) {
-        atomicOr(status, kStatusIterationLimit);
-        break;
-      }
-      const float4 s = __ldg(&T.nS[X]);
-      if (!(s.w > 0.0f)) continue;
-      ++cnt.visited;
-      const float4 a = __ldg(&T.nA[X]);
-      const float4 b = __ldg(&T.nB[X]);
-      const float ex = fmaxf(fmaxf(__fsub_rn(a.x, p.x), __fsub_rn(p.x, b.x)), 0.0f);
-      const float ey = fmaxf(fmaxf(__fsub_rn(a.y, p.y), __fsub_rn(p.y, b.y)), 0.0f);
-      const float ez = fmaxf(fmaxf(__fsub_rn(a.z, p.z), __fsub_rn(p.z, b.z)), 0.0f);
-      const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
-      if (__ldg(&T.nl2[X]) < __fmul_rn(P.theta2, r2)) {
-        F.add(rt.contribute(p.x, p.y, p.z, S, X, s.x, s.y, s.z, s.w));
-        continue;
-      }
-      const int4 t = __ldg(&T.nT[X]);
-      if (t.x < 0) {
-        for (int j = t.z; j < t.z + t.w; ++j) {
-          const float4 y = __ldg(&T.src[j]);
-          if (!(y.w > 0.0f)) continue;
-          F.add(rt.contribute(p.x, p.y, p.z, S, X, y.x, y.y, y.z, y.w));
+    // ray state
+    bool in_ray = false;
+    Ray R;
+    R.px = p.x;
+    R.py = p.y;
+    R.pz = p.z;
+    CSum tau;
+    float rayL = 0.0f, s2 = 0.0f;
+    int C = 0, dC = 0, dstar = 0, nb = 0, b = 0, rsp = 0;
+    // single sources of an opened leaf
+    int j = 0, j_end = 0, leafC = 0, dleaf = 0;
+    const int box_limit = 2 * T.n_nodes_cap + 4;
+    int boxes = 0;
+
+    while (true) {
+      if (in_ray) {
+        int box;
+        if (rsp > 0) {
+          box = rstack[--rsp];
+        } else if (b < nb) {
+          const int nS_side = dS - dstar - 1;  // siblings on the sink side
+          if (b == 0) box = S;
+          else if (b <= nS_side) box = anc[dS - b + 1] ^ 1;
+          else if (b == nS_side + 1) box = C;
+          else box = path[dC - (b - nS_side - 2)] ^ 1;
+          ++b;
+        } else {
+          const float t = tau.get();
+          F.add(rayL * expf(-t) / (12.566370614359172f * s2));
+          ++c_rays;
+          in_ray = false;
+          continue;
         }
-      } else {
-        if (sp + 2 > STACK) {
-          atomicOr(status, kStatusStackOverflow);
+        if (++boxes > box_limit) {
+          atomicOr(status, kStatusIterationLimit);
           break;
         }
-        stack[sp++] = t.x + 1;
-        stack[sp++] = t.x;
+        const float4 a = __ldg(&T.nA[box]);
+        const float4 bb = __ldg(&T.nB[box]);
+        const float l = clip_len(R, a, bb);
+        ++c_clip;
+        if (!(l > 0.0f)) continue;
+        if (P.tau_ref <= 0.0f || __fmul_rn(bb.w, l) > P.tau_ref) {
+          const int child = __ldg(&T.nT[box].x);
+          if (child >= 0) {
+            if (rsp + 2 > stack_limit) {
+              atomicOr(status, kStatusStackOverflow);
+              break;
+            }
+            ++c_ref;
+            rstack[rsp++] = child + 1;
+            rstack[rsp++] = child;
+            continue;
+          }
+        }
+        tau.add(a.w * l);
+        ++c_segs;
+        continue;
       }
+
+      // ---- walk step: next pseudo-source
+      float qx, qy, qz, L;
+      if (j < j_end) {
+        const float4 y = __ldg(&T.src[j]);
+        ++j;
+        if (!(y.w > 0.0f)) continue;
+        C = leafC;
+        dC = dleaf;
+        qx = y.x;
+        qy = y.y;
+        qz = y.z;
+        L = y.w;
+      } else {
+        if (sp == 0) break;
+        --sp;
+        const int X = wstack[sp];
+        const int dX = wdepth[sp];
+        path[dX] = X;
+        const unsigned long long bit = 1ull << dX;
+        on_path = (dX <= dS && anc[dX] == X) ? (on_path | bit) : (on_path & ~bit);
+        const float4 s = __ldg(&T.nS[X]);
+        if (!(s.w > 0.0f)) continue;
+        ++c_visit;
+        const float4 a = __ldg(&T.nA[X]);
+        const float4 bb = __ldg(&T.nB[X]);
+        const float ex = fmaxf(fmaxf(__fsub_rn(a.x, p.x), __fsub_rn(p.x, bb.x)), 0.0f);
+        const float ey = fmaxf(fmaxf(__fsub_rn(a.y, p.y), __fsub_rn(p.y, bb.y)), 0.0f);
+        const float ez = fmaxf(fmaxf(__fsub_rn(a.z, p.z), __fsub_rn(p.z, bb.z)), 0.0f);
+        const float r2 =
+            __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
+        if (!(__ldg(&T.nl2[X]) < __fmul_rn(P.theta2, r2))) {
+          const int4 t = __ldg(&T.nT[X]);
+          if (t.x < 0) {
+            j = t.z;
+            j_end = t.z + t.w;
+            leafC = X;
+            dleaf = dX;
+          } else {
+            if (sp + 2 > stack_limit) {
+              atomicOr(status, kStatusStackOverflow);
+              break;
+            }
+            wstack[sp] = t.x + 1;
+            wdepth[sp] = dX + 1;
+            wstack[sp + 1] = t.x;
+            wdepth[sp + 1] = dX + 1;
+            sp += 2;
+          }
+          continue;
+        }
+        C = X;
+        dC = dX;
+        qx = s.x;
+        qy = s.y;
+        qz = s.z;
+        L = s.w;
+      }
+      // ---- start the reverse ray from the sink to (q, L) in cell C
+      R.dx = __fsub_rn(qx, p.x);
+      R.dy = __fsub_rn(qy, p.y);
+      R.dz = __fsub_rn(qz, p.z);
+      s2 = __fadd_rn(__fadd_rn(__fmul_rn(R.dx, R.dx), __fmul_rn(R.dy, R.dy)),
+                     __fmul_rn(R.dz, R.dz));
+      if (s2 < P.smin2) continue;  // a source on top of the sink adds nothing
+      R.len = __fsqrt_rn(s2);
+      R.ix = R.dx != 0.0f ? __frcp_rn(R.dx) : 0.0f;
+      R.iy = R.dy != 0.0f ? __frcp_rn(R.dy) : 0.0f;
+      R.iz = R.dz != 0.0f ? __frcp_rn(R.dz) : 0.0f;
+      rayL = L;
+      tau = CSum();
+      b = 0;
+      rsp = 0;
+      boxes = 0;
+      if (C == S) {
+        nb = 1;
+      } else {
+        // depth of the lowest common ancestor: the common prefix of path and anc
+        const int mn = dC < dS ? dC : dS;
+        const unsigned long long m = on_path & ((2ull << mn) - 1ull);  // mn <= 62
+        dstar = __ffsll((long long)~m) - 2;
+        nb = dS + dC - 2 * dstar;
+      }
+      in_ray = true;
     }
     const int out = sink_idx ? k : T.perm[i];
     flux_out[out] = F.get();
-    if (counters) {
-      int4 c = make_int4(cnt.rays, cnt.segs, cnt.visited, cnt.refines);
-      reinterpret_cast<int4*>(counters)[out] = c;
-    }
+    if (counters)
+      reinterpret_cast<int4*>(counters)[out] = make_int4(c_rays, c_segs, c_visit, c_ref);
   }
   if (stats) {
-    unsigned long long v[5] = {(unsigned long long)cnt.rays, (unsigned long long)cnt.segs,
-                               (unsigned long long)cnt.visited, (unsigned long long)cnt.refines,
-                               (unsigned long long)cnt.clips};
+    unsigned long long v[5] = {(unsigned long long)c_rays, (unsigned long long)c_segs,
+                               (unsigned long long)c_visit, (unsigned long long)c_ref,
+                               (unsigned long long)c_clip};
 #pragma unroll
-    for (int j = 0; j < 5; ++j) {
-      unsigned long long x = v[j];
+    for (int q = 0; q < 5; ++q) {
+      unsigned long long x = v[q];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-      if ((threadIdx.x & 31) == 0 && x) atomicAdd(&stats[j], x);
+      if ((threadIdx.x & 31) == 0 && x) atomicAdd(&stats[q], x);
     }
   }
 }
@@ -253,15 +297,8 @@ cudaError_t launch_walk(const TreeView& T, const long long* sink_idx, int n_sink
   const int threads = 128;
   (void)block_size;
   const int blocks = (n_sink + threads - 1) / threads;
-  if (wp.stack_depth <= 4)  // only useful to exercise the overflow check
-    walk_plain_kernel<4><<<blocks, threads, 0, s>>>(T, sink_idx, n_sink, wp, flux_out, counters,
-                                                    stats, status);
-  else if (wp.stack_depth <= 32)
-    walk_plain_kernel<32><<<blocks, threads, 0, s>>>(T, sink_idx, n_sink, wp, flux_out, counters,
-                                                     stats, status);
-  else
-    walk_plain_kernel<64><<<blocks, threads, 0, s>>>(T, sink_idx, n_sink, wp, flux_out, counters,
-                                                     stats, status);
+  walk_flat_kernel<<<blocks, threads, 0, s>>>(T, sink_idx, n_sink, wp, flux_out, counters, stats,
+                                              status);
   note_launch();
   return cudaGetLastError();
 }
