@@ -60,7 +60,8 @@ typedef struct {
     float theta_open;
     float tau_ref;
     int bucket;
-    int sinks_per_warp; /* 0 = default */
+    int sinks_per_warp; /* sinks in each warp's chunk of the walk (a lane that finishes
+                           its sink takes the next of the chunk); 0 = default (128) */
     int block_size;     /* threads per block of the walk, 0 = default */
     int stack_depth;    /* traversal stack entries per sink, 0 = default (64) */
 } trevr_params;
@@ -125,6 +126,58 @@ int trevr_build_tree(const float* gas_xyz, const float* alpha, const float* weig
 int trevr_compute_flux(const trevr_tree* t, const long long* sink_idx, long long n_sink,
                        const trevr_params* prm, float* flux_out, int* sink_counters,
                        trevr_stats* stats, void* stream);
+
+/*
+ * Gradients of a scalar loss through the flux, with the decisions of the
+ * forward pass held fixed (the merge/open choices of Eq. openangle, the
+ * refinement choices of Eq. refcrit and the cells each ray touches): the
+ * adjoint of Eq. simpint with tau from Eqs. taui/tausum. Centres of
+ * luminosity move with the luminosities (c_C = sum L_j y_j / L_C, Sec.
+ * 2.2.1); cell absorption is sum(w alpha)/sum(w) (Sec. 2.3).
+ *
+ *   t, sink_idx, n_sink, prm  exactly as in the forward call whose fluxes were
+ *             differentiated (the walk is replayed with the same decisions).
+ *   grad_flux  n_sink floats: dLoss/dF at each sink (same order as flux_out).
+ *   grad_lum   n_src floats, caller order: dLoss/dL_j (overwritten).
+ *   grad_alpha n_gas floats, caller order: dLoss/dalpha_i (overwritten).
+ * Allocates its FP64 accumulators with cudaMallocAsync on `stream` and
+ * synchronises the stream before returning. Gradients with respect to the
+ * positions are not computed.
+ */
+int trevr_compute_flux_backward(const trevr_tree* t, const long long* sink_idx, long long n_sink,
+                                const trevr_params* prm, const float* grad_flux, float* grad_lum,
+                                float* grad_alpha, void* stream);
+
+/*
+ * Batched flux for many independent boxes (each its own tree) in ONE persistent
+ * launch: the sinks of all trees are cut into work items of prm->sinks_per_warp
+ * consecutive sinks (Morton order; a multiple of 32, 0 = 64), largest trees
+ * first, and every warp of a grid of (SM count x resident blocks) takes the
+ * next item from a device counter until none are left. Each sink's flux is the
+ * same computation as trevr_compute_flux (Eq. simpint over the opening-angle
+ * walk with tau_ref refinement), so the results are bit-identical to one plain
+ * call per tree with the same parameters.
+ *
+ *   trevr_batch_create: trees = host array of n_trees tree handles (they must
+ *             outlive the batch); uploads their views; synchronous.
+ *   trevr_compute_flux_batched:
+ *     prm       theta_open, tau_ref (all trees), sinks_per_warp (item size),
+ *               block_size (64, 128 or 256; 0 = 128).
+ *     flux_out  DEVICE array of n_trees device pointers; flux_out[b] receives
+ *               n_gas(b) floats in that tree's caller order.
+ *     stats     host pointer or NULL; non-NULL synchronises and fills totals.
+ *   With stats == NULL the call only enqueues a memset and one kernel on
+ *   `stream` (it can be captured in a CUDA graph once a first call with the
+ *   same sinks_per_warp has built the work items; changing sinks_per_warp
+ *   rebuilds them with a synchronous upload).
+ *   trevr_batch_check: synchronise and return the batch's device status.
+ */
+typedef struct trevr_batch trevr_batch;
+int trevr_batch_create(trevr_tree* const* trees, int n_trees, trevr_batch** out);
+int trevr_compute_flux_batched(trevr_batch* batch, const trevr_params* prm,
+                               float* const* flux_out, trevr_stats* stats, void* stream);
+int trevr_batch_check(const trevr_batch* batch, void* stream);
+void trevr_batch_free(trevr_batch* batch);
 
 /* Synchronise `stream` and return the first device error recorded on the tree
    since the last check (TREVR_OK if none), clearing it. */

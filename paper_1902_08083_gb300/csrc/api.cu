@@ -1,9 +1,12 @@
 // C ABI of libtrevr: argument checks, status mapping, dispatch to the kernels.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <numeric>
+#include <vector>
 
 #include "trevr.h"
 #include "trevr_internal.cuh"
@@ -35,6 +38,7 @@ static WalkParams walk_params(const trevr_tree* t, const trevr_params* prm) {
   volatile float smin = 1e-12f * t->side;
   wp.smin2 = smin * smin;
   wp.stack_depth = prm->stack_depth > 0 ? prm->stack_depth : kDefaultStack;
+  wp.sinks_per_warp = prm->sinks_per_warp;
   return wp;
 }
 
@@ -154,6 +158,195 @@ int trevr_compute_flux(const trevr_tree* t, const long long* sink_idx, long long
   return TREVR_OK;
 }
 
+int trevr_compute_flux_backward(const trevr_tree* t, const long long* sink_idx, long long n_sink,
+                                const trevr_params* prm, const float* grad_flux, float* grad_lum,
+                                float* grad_alpha, void* stream) {
+  if (!t || !params_ok(prm)) return TREVR_ERR_INVALID_ARGUMENT;
+  if (n_sink < 0 || n_sink > (1ll << 30)) return TREVR_ERR_INVALID_ARGUMENT;
+  if (n_sink > 0 && !grad_flux) return TREVR_ERR_INVALID_ARGUMENT;
+  if (n_sink > 0 && !sink_idx && n_sink != t->n_gas) return TREVR_ERR_INVALID_ARGUMENT;
+  if ((t->n_src > 0 && !grad_lum) || !grad_alpha) return TREVR_ERR_INVALID_ARGUMENT;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nc = (size_t)t->n_nodes + 1, ns = (size_t)(t->n_src > 0 ? t->n_src : 1);
+  // accumulators: G, a, b (3 per cell), e (per source), H (per cell prefix)
+  const size_t words = 5 * nc + ns + nc;
+  double* buf = nullptr;
+  cudaError_t err = cudaMallocAsync((void**)&buf, words * sizeof(double), s);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return TREVR_ERR_OUT_OF_MEMORY;
+  }
+  cudaMemsetAsync(buf, 0, words * sizeof(double), s);
+  AdjointArgs J;
+  J.grad_flux = grad_flux;
+  J.G = buf;
+  J.a = buf + nc;
+  J.b = buf + 2 * nc;
+  J.e = buf + 5 * nc;
+  double* H = buf + 5 * nc + ns;
+  WalkParams wp = walk_params(t, prm);
+  err = launch_walk_adjoint(t->view(), sink_idx, (int)n_sink, wp, J, t->status, s);
+  if (err == cudaSuccess) err = adjoint_finalize(t, J, grad_lum, grad_alpha, H, s);
+  cudaFreeAsync(buf, s);
+  if (err != cudaSuccess) return cuda_to_error(err);
+  int status = 0;
+  cudaMemcpyAsync(&status, t->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) return cuda_to_error(err);
+  if (status) {
+    cudaMemsetAsync(t->status, 0, sizeof(int), s);
+    cudaStreamSynchronize(s);
+    return status_to_error(status);
+  }
+  return TREVR_OK;
+}
+
+int trevr_batch_create(trevr_tree* const* trees, int n_trees, trevr_batch** out) {
+  if (!out) return TREVR_ERR_INVALID_ARGUMENT;
+  *out = nullptr;
+  if (!trees || n_trees < 1) return TREVR_ERR_INVALID_ARGUMENT;
+  for (int b = 0; b < n_trees; ++b)
+    if (!trees[b]) return TREVR_ERR_INVALID_ARGUMENT;
+  trevr_batch* B = new trevr_batch();
+  std::memset(B, 0, sizeof(*B));
+  cudaGetDevice(&B->device);
+  cudaDeviceGetAttribute(&B->n_sm, cudaDevAttrMultiProcessorCount, B->device);
+  B->n_trees = n_trees;
+  B->h_sizes = new long long[n_trees];
+  std::vector<TreeView> views(n_trees);
+  for (int b = 0; b < n_trees; ++b) {
+    views[b] = trees[b]->view();
+    B->h_sizes[b] = trees[b]->n_gas;
+    B->n_sinks += trees[b]->n_gas;
+  }
+  cudaError_t e = cudaMalloc(&B->views, sizeof(TreeView) * n_trees);
+  if (e == cudaSuccess) e = cudaMalloc(&B->counter, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMalloc(&B->status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&B->d_stats, 8 * sizeof(unsigned long long));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(B->views, views.data(), sizeof(TreeView) * n_trees, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(B->status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    trevr_batch_free(B);
+    cudaGetLastError();
+    return cuda_to_error(e);
+  }
+  *out = B;
+  return TREVR_OK;
+}
+
+// (Re)build the work items for `item` sinks per item: trees in decreasing size, so
+// the largest boxes start first and the small ones fill the tail.
+static int batch_items(trevr_batch* B, int item) {
+  if (B->items && B->item == item) return TREVR_OK;
+  std::vector<int> order(B->n_trees);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return B->h_sizes[a] > B->h_sizes[b]; });
+  std::vector<int2> items;
+  for (int b : order)
+    for (long long f = 0; f < B->h_sizes[b]; f += item) items.push_back(make_int2(b, (int)f));
+  if (B->items) cudaFree(B->items);
+  B->items = nullptr;
+  cudaError_t e = cudaMalloc(&B->items, sizeof(int2) * (items.empty() ? 1 : items.size()));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(B->items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_to_error(e);
+  B->item = item;
+  B->n_items = (int)items.size();
+  return TREVR_OK;
+}
+
+int trevr_compute_flux_batched(trevr_batch* B, const trevr_params* prm, float* const* flux_out,
+                               trevr_stats* stats, void* stream) {
+  if (!B || !flux_out || !params_ok(prm)) return TREVR_ERR_INVALID_ARGUMENT;
+  const int item = prm->sinks_per_warp > 0 ? prm->sinks_per_warp : 64;
+  if (item % 32 != 0 || item > (1 << 20)) return TREVR_ERR_INVALID_ARGUMENT;
+  int rc = batch_items(B, item);
+  if (rc != TREVR_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  WalkParams wp;
+  {
+    volatile float th = prm->theta_open;
+    wp.theta2 = th * th;
+  }
+  wp.tau_ref = prm->tau_ref;
+  wp.stack_depth = prm->stack_depth > 0 ? prm->stack_depth : kDefaultStack;
+  wp.smin2 = 0.0f;  // set per tree by the kernel from the tree's side
+  wp.sinks_per_warp = item;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    cudaMemsetAsync(B->d_stats, 0, 5 * sizeof(unsigned long long), s);
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+  }
+  const int bs = prm->block_size > 0 ? prm->block_size : 128;
+  cudaError_t err = launch_walk_batched(B->views, flux_out, B->items, B->n_items, item, B->counter,
+                                        wp, stats ? B->d_stats : nullptr, B->status, bs, B->n_sm,
+                                        s);
+  if (err != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return cuda_to_error(err);
+  }
+  if (!stats) return TREVR_OK;
+  cudaEventRecord(e1, s);
+  unsigned long long h[5];
+  int status = 0;
+  cudaMemcpyAsync(h, B->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&status, B->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  err = cudaStreamSynchronize(s);
+  float ms = 0.0f;
+  if (err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return cuda_to_error(err);
+  stats->interactions = (long long)h[0];
+  stats->segments = (long long)h[1];
+  stats->src_nodes_visited = (long long)h[2];
+  stats->refine_expansions = (long long)h[3];
+  stats->cells_clipped = (long long)h[4];
+  stats->walk_ms = ms;
+  if (status) {
+    cudaMemsetAsync(B->status, 0, sizeof(int), s);
+    cudaStreamSynchronize(s);
+    return status_to_error(status);
+  }
+  return TREVR_OK;
+}
+
+int trevr_batch_check(const trevr_batch* B, void* stream) {
+  if (!B) return TREVR_ERR_INVALID_ARGUMENT;
+  cudaStream_t s = (cudaStream_t)stream;
+  int status = 0;
+  cudaMemcpyAsync(&status, B->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaError_t err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) return cuda_to_error(err);
+  if (status) {
+    cudaMemsetAsync(B->status, 0, sizeof(int), s);
+    cudaStreamSynchronize(s);
+  }
+  return status_to_error(status);
+}
+
+void trevr_batch_free(trevr_batch* B) {
+  if (!B) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(B->device);
+  cudaDeviceSynchronize();
+  if (B->views) cudaFree(B->views);
+  if (B->items) cudaFree(B->items);
+  if (B->counter) cudaFree(B->counter);
+  if (B->status) cudaFree(B->status);
+  if (B->d_stats) cudaFree(B->d_stats);
+  delete[] B->h_sizes;
+  cudaSetDevice(cur);
+  delete B;
+}
+
 int trevr_check(const trevr_tree* t, void* stream) {
   if (!t) return TREVR_ERR_INVALID_ARGUMENT;
   cudaStream_t s = (cudaStream_t)stream;
@@ -248,7 +441,7 @@ void trevr_tree_free(trevr_tree* t) {
   void* ptrs[] = {t->key, t->perm,   t->rank,   t->leaf_of, t->pos,    t->w,      t->nA,
                   t->nB,  t->nS,     t->nT,     t->nl2,     t->ndepth, t->nfirst, t->ncount,
                   t->nglo, t->nghi,  t->src,    t->src_order, t->levels, t->d_n_nodes,
-                  t->status, t->d_stats};
+                  t->status, t->d_stats, t->src_leaf, t->nW};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   cudaSetDevice(cur);

@@ -391,13 +391,16 @@ __global__ void src_leaf_kernel(const float* __restrict__ xyz, const float* __re
 }
 
 __global__ void gather_sources_kernel(const float* __restrict__ xyz, const float* __restrict__ lum,
-                                      int n_src, const unsigned* __restrict__ order, float4* src,
-                                      int* src_order) {
+                                      int n_src, const unsigned* __restrict__ order,
+                                      const unsigned long long* __restrict__ leaf_first,
+                                      const int* __restrict__ leaf_of, float4* src, int* src_order,
+                                      int* src_leaf) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_src) return;
   int o = (int)order[k];
   src[k] = make_float4(xyz[o], xyz[(size_t)n_src + o], xyz[2 * (size_t)n_src + o], lum[o]);
   src_order[k] = o;
+  src_leaf[k] = leaf_of[(int)leaf_first[k]];  // the leaf that starts at that particle
 }
 
 __device__ __forceinline__ int lower_bound_u64(const unsigned long long* a, int n,
@@ -443,6 +446,7 @@ struct MomentArrays {
   const float4* src;
   const int* levels;
   Moments* mom;
+  double* nW;
   float4* nA;
   float4* nB;
   float4* nS;
@@ -514,6 +518,7 @@ __global__ void moments_level_kernel(MomentArrays A, int L) {
       }
     }
     A.mom[X] = m;
+    A.nW[X] = m.W;
     const double amin = fmin(fmin(m.amin[0], m.amin[1]), m.amin[2]);
     const double amax = fmax(fmax(m.amax[0], m.amax[1]), m.amax[2]);
     const float abar = __double2float_rn(__ddiv_rn(m.WA, m.W));
@@ -611,6 +616,7 @@ int build_tree_impl(const float* gas_xyz, const float* alpha, const float* weigh
   t->ndepth = keep.get<int>(cap);
   t->src = keep.get<float4>(ns);
   t->src_order = keep.get<int>(ns);
+  t->src_leaf = keep.get<int>(ns);
   t->levels = keep.get<int>(2 * kMaxLevels);
   t->d_n_nodes = keep.get<int>(1);
   t->status = keep.get<int>(1);
@@ -700,6 +706,7 @@ int build_tree_impl(const float* gas_xyz, const float* alpha, const float* weigh
   const int end_cells = levels[2 * max_depth + 1];
   t->n_nodes = end_cells - kRoot;
   t->max_depth = max_depth;
+  for (int l = 0; l < 2 * kMaxLevels; ++l) t->h_levels[l] = levels[l];
 
   // 3. sources
   if (ns > 0) {
@@ -707,8 +714,9 @@ int build_tree_impl(const float* gas_xyz, const float* alpha, const float* weigh
                                                        t->nfirst, skeys, svals, t->status);
     note_launch();
     radix_sort(skeys, svals, ns, 32, SS, s);
-    gather_sources_kernel<<<grid_for(ns, 256), 256, 0, s>>>(src_xyz, src_lum, ns, svals, t->src,
-                                                             t->src_order);
+    gather_sources_kernel<<<grid_for(ns, 256), 256, 0, s>>>(src_xyz, src_lum, ns, svals, skeys,
+                                                             t->leaf_of, t->src, t->src_order,
+                                                             t->src_leaf);
     note_launch();
     node_src_range_kernel<<<grid_for(end_cells - kRoot, 256), 256, 0, s>>>(
         end_cells, t->nfirst, t->ncount, skeys, ns, t->nT);
@@ -720,6 +728,7 @@ int build_tree_impl(const float* gas_xyz, const float* alpha, const float* weigh
   t->nB = keep.get<float4>(ncell);
   t->nS = keep.get<float4>(ncell);
   t->nl2 = keep.get<float>(ncell);
+  t->nW = keep.get<double>(ncell);
   Moments* mom = tmp.get<Moments>(ncell);
   if (!keep.ok || !tmp.ok) {
     cudaGetLastError();
@@ -730,6 +739,7 @@ int build_tree_impl(const float* gas_xyz, const float* alpha, const float* weigh
   cudaMemsetAsync(t->nB, 0, sizeof(float4), s);
   cudaMemsetAsync(t->nS, 0, sizeof(float4), s);
   cudaMemsetAsync(t->nl2, 0, sizeof(float), s);
+  cudaMemsetAsync(t->nW, 0, sizeof(double), s);
   MomentArrays MA;
   MA.nT = t->nT;
   MA.nglo = t->nglo;
@@ -741,6 +751,7 @@ int build_tree_impl(const float* gas_xyz, const float* alpha, const float* weigh
   MA.src = t->src;
   MA.levels = t->levels;
   MA.mom = mom;
+  MA.nW = t->nW;
   MA.nA = t->nA;
   MA.nB = t->nB;
   MA.nS = t->nS;

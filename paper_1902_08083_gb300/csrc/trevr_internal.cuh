@@ -7,6 +7,10 @@
 #include "trevr.h"
 
 namespace trevr {
+struct TreeView;
+}
+
+namespace trevr {
 
 constexpr int kGridBits = 21;
 constexpr int kGridMax = 1 << kGridBits;  // cells per axis of the integer grid
@@ -14,6 +18,7 @@ constexpr int kRoot = 1;                  // breadth-first numbering, root at 1
 constexpr int kMaxLevels = 66;            // depth <= 63 (one key bit per cut), plus slack
 constexpr int kDefaultStack = 64;         // >= max depth + 1: a walk can never overflow it
 constexpr int kMaxStack = 128;
+constexpr int kDefaultChunk = 128;        // sinks per warp of the walk
 
 // device status bits (OR-ed by kernels, mapped to TREVR_ERR_* on the host)
 constexpr int kStatusOutOfDomain = 1;
@@ -50,6 +55,20 @@ struct TreeView {
 
 }  // namespace trevr
 
+// Batch of independent trees for the persistent launch (host object behind the C handle).
+struct trevr_batch {
+  int device, n_trees, n_sm;
+  int item;           // sinks per work item (current)
+  int n_items;
+  long long n_sinks;  // all gas particles of all trees
+  trevr::TreeView* views;  // device, n_trees
+  int2* items;             // device, work items (tree, first sorted sink)
+  unsigned* counter;       // device work counter
+  int* status;             // device status word
+  unsigned long long* d_stats;
+  long long* h_sizes;      // host, particles per tree
+};
+
 // Host-side tree object behind the opaque C handle.
 struct trevr_tree {
   int device;
@@ -79,6 +98,9 @@ struct trevr_tree {
   // sources
   float4* src;
   int* src_order;
+  int* src_leaf;  // leaf cell of each sorted source
+  double* nW;     // sum of the volume weights of each cell (for the adjoint)
+  int h_levels[2 * trevr::kMaxLevels];  // host copy of the level ranges
   // bookkeeping
   int* levels;    // kMaxLevels x 2 (begin, end)
   int* d_n_nodes;
@@ -115,11 +137,31 @@ struct WalkParams {
   float tau_ref;
   float smin2;   // (1e-12 side)^2 (fp32): coincident-source cut
   int stack_depth;
+  int sinks_per_warp;  // sinks in each warp's chunk (0 = default)
 };
+// accumulators of the adjoint (FP64, zeroed by the caller)
+struct AdjointArgs {
+  const float* grad_flux;  // dLoss/dF per sink, caller order of the sinks
+  double* G;               // per cell: sum of -g f l over segments using the cell
+  double* a;               // per cell: sum of g f / L_C over merged interactions
+  double* b;               // per cell, 3: sum of g grad_q f / L_C
+  double* e;               // per sorted source: sum of g f / L_j over single-source rays
+};
+cudaError_t launch_walk_adjoint(const TreeView& T, const long long* sink_idx, int n_sink,
+                                const WalkParams& wp, const AdjointArgs& J, int* status,
+                                cudaStream_t s);
+cudaError_t launch_walk_batched(const TreeView* views, float* const* flux_out, const int2* items,
+                                int n_items, int item, unsigned* counter, const WalkParams& wp,
+                                unsigned long long* stats, int* status, int block_size,
+                                int n_sm, cudaStream_t s);
 cudaError_t launch_walk(const TreeView& T, const long long* sink_idx, int n_sink,
                         const WalkParams& wp, float* flux_out, int* counters,
                         unsigned long long* stats, int* status, int block_size,
                         cudaStream_t s);
+
+// ---- adjoint.cu: from the cell accumulators to the caller's gradients
+cudaError_t adjoint_finalize(const trevr_tree* t, const AdjointArgs& J, float* grad_lum,
+                             float* grad_alpha, double* H, cudaStream_t s);
 
 // ---- api.cu helpers
 int status_to_error(int status_bits);

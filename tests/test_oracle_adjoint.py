@@ -52,8 +52,8 @@ def test_adjoint_matches_replay_finite_differences(oracle_lib, theta, tau_ref, w
 def fd_agrees(R, w, kind, idx, val, ref, rel=1e-3, tol=1e-3):
     """Central difference with step rel*val agrees with ref to tol (relative). The frozen
     loss is piecewise smooth (a ray's entry or exit plane can switch inside the step), so
-    a step that straddles such a kink is retried with a 10x smaller step."""
-    for r in (rel, rel / 10):
+    a step that straddles such a kink is retried with smaller steps (down to 1e-6)."""
+    for r in (rel, rel / 10, rel / 100, rel / 1000):
         h = r * val
         fd = (R.loss(w, kind, idx, h) - R.loss(w, kind, idx, -h)) / (2 * h)
         if abs(fd - ref) <= tol * abs(ref) + 1e-9:
