@@ -5,8 +5,8 @@ tree-based reverse ray tracer for radiative transfer. The CUDA library
 ``libtrevr.so`` (C ABI in ``include/trevr.h``) builds the radiation tree and
 computes the flux at every sink; ``trevr.py`` is a thin ctypes binding.
 """
-from .trevr import (Tree, TrevrError, build_tree, check, compute_flux,  # noqa: F401
-                    load_library, make_params)
+from .trevr import (Batch, Tree, TrevrError, TrevrFlux, build_tree, check, compute_flux,  # noqa: F401
+                    compute_flux_backward, load_library, make_params, trevr_flux)
 
-__all__ = ["Tree", "TrevrError", "build_tree", "check", "compute_flux", "load_library",
-           "make_params"]
+__all__ = ["Batch", "Tree", "TrevrError", "TrevrFlux", "build_tree", "check", "compute_flux",
+           "compute_flux_backward", "load_library", "make_params", "trevr_flux"]

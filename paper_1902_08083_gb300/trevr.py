@@ -28,9 +28,11 @@ ERRORS = {
 
 # names of every entry point declared in include/trevr.h
 EXPORTS = (
-    "trevr_build_tree", "trevr_compute_flux", "trevr_check", "trevr_tree_info",
+    "trevr_build_tree", "trevr_compute_flux", "trevr_compute_flux_backward", "trevr_check",
+    "trevr_tree_info",
     "trevr_tree_export", "trevr_tree_free", "trevr_status_string", "trevr_kernel_launches",
-    "trevr_morton_sort_noalloc",
+    "trevr_morton_sort_noalloc", "trevr_batch_create", "trevr_compute_flux_batched",
+    "trevr_batch_check", "trevr_batch_free",
 )
 NOALLOC_MAX_N = 1 << 20
 
@@ -84,6 +86,18 @@ def load_library(path: str = LIB_PATH):
         lib.trevr_compute_flux.argtypes = [P, P, ll, ctypes.POINTER(Params), P, P,
                                            ctypes.POINTER(Stats), P]
         lib.trevr_compute_flux.restype = ctypes.c_int
+        lib.trevr_compute_flux_backward.argtypes = [P, P, ll, ctypes.POINTER(Params), P, P, P,
+                                                    P]
+        lib.trevr_compute_flux_backward.restype = ctypes.c_int
+        lib.trevr_batch_create.argtypes = [P, ctypes.c_int, ctypes.POINTER(P)]
+        lib.trevr_batch_create.restype = ctypes.c_int
+        lib.trevr_compute_flux_batched.argtypes = [P, ctypes.POINTER(Params), P,
+                                                   ctypes.POINTER(Stats), P]
+        lib.trevr_compute_flux_batched.restype = ctypes.c_int
+        lib.trevr_batch_check.argtypes = [P, P]
+        lib.trevr_batch_check.restype = ctypes.c_int
+        lib.trevr_batch_free.argtypes = [P]
+        lib.trevr_batch_free.restype = None
         lib.trevr_check.argtypes = [P, P]
         lib.trevr_check.restype = ctypes.c_int
         lib.trevr_tree_info.argtypes = [P, ctypes.POINTER(ll), ctypes.POINTER(ctypes.c_int),
@@ -256,6 +270,129 @@ def morton_sort_noalloc(gas_xyz, lo=(0.0, 0.0, 0.0), side=1.0, keys_out=None, pe
     if rc != TREVR_OK:
         raise TrevrError(rc, "trevr_morton_sort_noalloc")
     return keys_out, perm_out
+
+
+def compute_flux_backward(tree: Tree, grad_flux, theta=0.75, tau_ref=0.1, sink_idx=None,
+                          stream=None, **tuning):
+    """Adjoint of compute_flux with the forward decisions frozen (trevr_compute_flux_backward).
+    Returns (grad_lum[n_src], grad_alpha[n_gas]) in the caller's order."""
+    lib = tree._lib
+    n = tree.n_gas if sink_idx is None else int(sink_idx.shape[0])
+    grad_flux = grad_flux.contiguous().to(torch.float32)
+    if grad_flux.numel() != n:
+        raise ValueError(f"grad_flux has {grad_flux.numel()} elements, expected {n}")
+    gl = torch.empty(tree.n_src, dtype=torch.float32, device=tree.device)
+    ga = torch.empty(tree.n_gas, dtype=torch.float32, device=tree.device)
+    prm = make_params(theta, tau_ref, tree.bucket, **tuning)
+    rc = lib.trevr_compute_flux_backward(
+        tree.handle, _dev_ptr(sink_idx, torch.int64, "sink_idx"), n, ctypes.byref(prm),
+        _dev_ptr(grad_flux, torch.float32, "grad_flux"),
+        _dev_ptr(gl, torch.float32, "grad_lum") if tree.n_src else None,
+        _dev_ptr(ga, torch.float32, "grad_alpha"), _stream_ptr(stream))
+    if rc != TREVR_OK:
+        raise TrevrError(rc, "trevr_compute_flux_backward")
+    return gl, ga
+
+
+class TrevrFlux(torch.autograd.Function):
+    """Flux at every gas particle as a differentiable function of the absorption
+    coefficients alpha and the source luminosities (positions are not differentiated).
+    The backward pass is the library's adjoint with the forward decisions frozen."""
+
+    @staticmethod
+    def forward(ctx, gas_xyz, alpha, src_xyz, src_lum, theta, tau_ref, bucket, lo, side, weight):
+        tree = build_tree(gas_xyz.detach(), alpha.detach().contiguous(), src_xyz.detach(),
+                          src_lum.detach().contiguous(),
+                          None if weight is None else weight.detach(), lo, side, bucket)
+        flux = compute_flux(tree, theta, tau_ref)
+        ctx.tree = tree
+        ctx.theta, ctx.tau_ref = theta, tau_ref
+        return flux
+
+    @staticmethod
+    def backward(ctx, grad_flux):
+        gl, ga = compute_flux_backward(ctx.tree, grad_flux, ctx.theta, ctx.tau_ref)
+        ctx.tree.free()
+        return None, ga, None, gl, None, None, None, None, None, None
+
+
+def trevr_flux(gas_xyz, alpha, src_xyz, src_lum, theta=0.75, tau_ref=0.1, bucket=8,
+               lo=(0.0, 0.0, 0.0), side=1.0, weight=None):
+    """Differentiable flux (see TrevrFlux)."""
+    return TrevrFlux.apply(gas_xyz, alpha, src_xyz, src_lum, theta, tau_ref, bucket, lo, side,
+                           weight)
+
+
+class Batch:
+    """Independent trees processed by one persistent launch (trevr_batch_create).
+
+    Owns one fp32 flux tensor per tree (caller order) and the device array of their
+    pointers, so a call only enqueues device work and can be captured in a CUDA graph."""
+
+    def __init__(self, trees):
+        lib = load_library()
+        self._lib = lib
+        self._h = None
+        self.trees = list(trees)
+        arr = (ctypes.c_void_p * len(self.trees))(*[t.handle.value for t in self.trees])
+        h = ctypes.c_void_p()
+        rc = lib.trevr_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(self.trees),
+                                    ctypes.byref(h))
+        if rc != TREVR_OK:
+            raise TrevrError(rc, "trevr_batch_create")
+        self._h = h
+        dev = self.trees[0].device
+        self.flux = [torch.empty(t.n_gas, dtype=torch.float32, device=dev) for t in self.trees]
+        self._ptrs = torch.tensor([f.data_ptr() for f in self.flux], dtype=torch.int64,
+                                  device=dev)
+        self.n_sinks = sum(t.n_gas for t in self.trees)
+        self.graph = None
+
+    def run(self, theta=0.75, tau_ref=0.1, stats=False, stream=None, **tuning):
+        """Enqueue the batched flux (results in self.flux); stats=True synchronises."""
+        prm = make_params(theta, tau_ref, self.trees[0].bucket, **tuning)
+        st = Stats() if stats else None
+        rc = self._lib.trevr_compute_flux_batched(self._h, ctypes.byref(prm),
+                                                  ctypes.c_void_p(self._ptrs.data_ptr()),
+                                                  ctypes.byref(st) if st is not None else None,
+                                                  _stream_ptr(stream))
+        if rc != TREVR_OK:
+            raise TrevrError(rc, "trevr_compute_flux_batched")
+        return st.as_dict() if stats else None
+
+    def capture(self, theta=0.75, tau_ref=0.1, **tuning):
+        """Capture one batched call in a CUDA graph (after a first call with the same
+        tuning has built the work items); replay with self.replay()."""
+        self.run(theta, tau_ref, **tuning)  # builds the work items outside the capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                self.run(theta, tau_ref, stream=s, **tuning)
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
+    def check(self, stream=None):
+        rc = self._lib.trevr_batch_check(self._h, _stream_ptr(stream))
+        if rc != TREVR_OK:
+            raise TrevrError(rc, "trevr_batch_check")
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            self._lib.trevr_batch_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def kernel_launches() -> int:
