@@ -184,6 +184,88 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _time_ms(fn, reps, stream):
+    import torch
+    out = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def _bench_batched(args):
+    """64 independent boxes (2^12..2^17 particles, log-uniform): one persistent launch
+    replayed from a CUDA graph, launch shape from the autotuner, vs 64 plain calls."""
+    import torch
+    from paper_1902_08083_gb300 import autotune, trevr
+    boxes = workloads.batched_boxes()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    trees = []
+    for P in boxes:
+        g = {k: torch.from_numpy(np.ascontiguousarray(P[k])).to(dev)
+             for k in ("gas_xyz", "alpha", "src_xyz", "src_lum")}
+        trees.append(trevr.build_tree(g["gas_xyz"], g["alpha"], g["src_xyz"], g["src_lum"],
+                                      lo=P["lo"], side=P["side"], bucket=P["bucket"]))
+    th, tr = boxes[0]["theta"], boxes[0]["tau_ref"]
+    B = trevr.Batch(trees)
+    tune = autotune.tune(B, th, tr)
+    shape = dict(sinks_per_warp=tune["sinks_per_warp"], block_size=tune["block_size"])
+    B.capture(th, tr, **shape)
+    for _ in range(args.warmup):
+        B.replay()
+    t_graph = _time_ms(B.replay, args.steps, stream)
+    outs = [torch.empty(t.n_gas, device=dev) for t in trees]
+
+    def sequential():
+        for t, o in zip(trees, outs):
+            trevr.compute_flux(t, th, tr, out=o)
+    sequential()
+    t_seq = _time_ms(sequential, args.steps, stream)
+    same = all(torch.equal(a, b) for a, b in zip(B.flux, outs))
+    n = B.n_sinks
+    res = {"workload": f"{len(trees)} boxes, {n} sinks (2^12..2^17 each), theta 0.75, tau_ref 0.1",
+           "graph_fluxes_per_s": n / (min(t_graph) * 1e-3),
+           "sequential_fluxes_per_s": n / (min(t_seq) * 1e-3),
+           "speedup": min(t_seq) / min(t_graph), "bit_equal_to_sequential": bool(same),
+           "launch_shape": shape, "tuned_from_cache": bool(tune.get("cached"))}
+    B.free()
+    for t in trees:
+        t.free()
+    return res
+
+
+def _bench_adjoint(args):
+    """Forward + adjoint on 2^21 particles / 1024 sources (lognormal sigma_ln=1),
+    loss sum_p w_p log F_p over every sink."""
+    import torch
+    from paper_1902_08083_gb300 import trevr
+    P = workloads.adjoint_problem()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    g = {k: torch.from_numpy(np.ascontiguousarray(P[k])).to(dev)
+         for k in ("gas_xyz", "alpha", "src_xyz", "src_lum")}
+    tree = trevr.build_tree(g["gas_xyz"], g["alpha"], g["src_xyz"], g["src_lum"], lo=P["lo"],
+                            side=P["side"], bucket=P["bucket"])
+    n = tree.n_gas
+    w = torch.from_numpy(P["loss_weight"]).to(dev)
+    F = trevr.compute_flux(tree, P["theta"], P["tau_ref"])
+    gflux = (w / F).contiguous()
+    fwd = _time_ms(lambda: trevr.compute_flux(tree, P["theta"], P["tau_ref"], out=F),
+                   args.steps, stream)
+    bwd = _time_ms(lambda: trevr.compute_flux_backward(tree, gflux, P["theta"], P["tau_ref"]),
+                   args.steps, stream)
+    tree.free()
+    return {"workload": f"{n} gas, {P['src_xyz'].shape[1]} sources, lognormal sigma_ln=1",
+            "forward_ms": min(fwd), "backward_ms": min(bwd),
+            "backward_sinks_per_s": n / (min(bwd) * 1e-3)}
+
+
 def run_ours(args):
     import torch
     from paper_1902_08083_gb300 import trevr
@@ -302,7 +384,7 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     achieved = alg_bytes / t_walk / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "walk_plain_kernel",
+                "frac": achieved / peak, "traffic": None, "kernel": "walk_kernel<false> (sink walk + rays + flux)",
                 "peak_kind": f"{peak_kind} (copy bandwidth, burst)",
                 "bytes_per_launch": alg_bytes}
 
@@ -322,6 +404,10 @@ def run_ours(args):
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "clocks": clk}
 
+    if world == 1 and not args.no_extras:
+        line["batched"] = _bench_batched(args)
+        line["adjoint"] = _bench_adjoint(args)
+
     if world == 1 and not args.no_cpu_baseline:
         info, sinks, fo, _ = _oracle_baseline(P, n, args.cpu_sample)
         fg = flux.cpu().numpy()[sinks].astype(np.float64)
@@ -337,8 +423,8 @@ def run_ours(args):
 
 
 def run_profile(args):
-    """A short program for ncu: one tree build, then the walk twice on a seeded sample
-    of sinks (the second launch is the one to capture)."""
+    """A short program for ncu: one tree build, then the walk twice on a contiguous
+    Morton-ordered run of sinks (the second launch is the one to capture)."""
     import torch
     from paper_1902_08083_gb300 import trevr
     torch.cuda.set_device(0)
@@ -350,7 +436,10 @@ def run_profile(args):
     tree = trevr.build_tree(g["gas_xyz"], g["alpha"], g["src_xyz"], g["src_lum"], lo=P["lo"],
                             side=P["side"], bucket=P["bucket"])
     m = min(n, args.sink_sample) if args.sink_sample > 0 else n
-    sinks = torch.from_numpy(workloads.sink_sample(n, m, seed=11)).to(dev)
+    # a contiguous run of sinks in Morton order (what the full walk's warps see)
+    perm = tree.export()["perm"]
+    start = (n - m) // 2
+    sinks = perm[start:start + m].to(torch.int64).contiguous()
     for _ in range(2):
         f = trevr.compute_flux(tree, P["theta"], P["tau_ref"], sink_idx=sinks)
     torch.cuda.synchronize()
@@ -369,9 +458,11 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=2048)
     ap.add_argument("--ref-sample", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched (64 boxes) and adjoint (2^21) measurements")
     ap.add_argument("--profile", action="store_true",
                     help="build once and run the walk twice on --sink-sample sinks (for ncu)")
-    ap.add_argument("--sink-sample", type=int, default=1 << 18)
+    ap.add_argument("--sink-sample", type=int, default=1 << 20)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

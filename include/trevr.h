@@ -61,7 +61,7 @@ typedef struct {
     float tau_ref;
     int bucket;
     int sinks_per_warp; /* sinks in each warp's chunk of the walk (a lane that finishes
-                           its sink takes the next of the chunk); 0 = default (128) */
+                           its sink takes the next of the chunk); 0 = default (32) */
     int block_size;     /* threads per block of the walk, 0 = default */
     int stack_depth;    /* traversal stack entries per sink, 0 = default (64) */
 } trevr_params;

@@ -18,7 +18,7 @@ constexpr int kRoot = 1;                  // breadth-first numbering, root at 1
 constexpr int kMaxLevels = 66;            // depth <= 63 (one key bit per cut), plus slack
 constexpr int kDefaultStack = 64;         // >= max depth + 1: a walk can never overflow it
 constexpr int kMaxStack = 128;
-constexpr int kDefaultChunk = 128;        // sinks per warp of the walk
+constexpr int kDefaultChunk = 32;         // sinks per warp of the walk (one per lane)
 
 // device status bits (OR-ed by kernels, mapped to TREVR_ERR_* on the host)
 constexpr int kStatusOutOfDomain = 1;

@@ -1,28 +1,33 @@
 // Sink walk, reverse ray and flux sum (Grond et al. 2019, Sec. 2.2.1-2.2.3).
 //
-// One lane per sink; sinks in Morton order, so the 32 sinks of a warp are
-// neighbours in space and walk almost the same cells. Per sink:
+// Per sink (a gas particle at p in leaf S):
 //   * source walk: a cell with L > 0 is merged into one pseudo-source at its
 //     centre of luminosity when theta_open > l/r (Eq. openangle), tested as
 //     l^2 < theta^2 r^2 in fp32; otherwise it is opened, and an opened leaf
 //     gives its sources one by one;
-//   * reverse ray to each pseudo-source: the segments are the sink's leaf S,
-//     the pseudo-source's cell C and the siblings of the cells on the two
-//     paths up to the children of their lowest common ancestor A; each segment
-//     uses the cell's mean absorption unless (alpha_max - alpha_min) * l >
-//     tau_ref (Eq. refcrit), in which case its children are used instead;
+//   * reverse ray to each pseudo-source: the segments are S, the pseudo-source's
+//     cell C and the siblings of the cells on the two paths up to the children
+//     of their lowest common ancestor A; each segment uses the cell's mean
+//     absorption unless (alpha_max - alpha_min) * l > tau_ref (Eq. refcrit), in
+//     which case its children are used instead;
 //   * flux: sum of L exp(-tau) / (4 pi s^2) (Eq. simpint).
-// The decisions (opening angle, refinement, "does the ray touch the cell")
-// are evaluated with explicitly rounded fp32 operations in a fixed order.
+// The decisions (opening angle, refinement, "does the ray touch the cell") are
+// evaluated with explicitly rounded fp32 operations in a fixed order.
 //
-// GPU form. Every lane runs one flat loop whose iterations are either one
-// walk step or one cell clip, so the lanes of a warp stay converged on the
-// clip work, which dominates (tens of clips per ray). The ancestors of the
-// sink's leaf are listed once per sink, and the walk keeps its depth-first
-// path, so the segment list of a ray is known without chasing parent links:
-// the sibling of a cell is its index XOR 1 (children are allocated in pairs),
-// and the common ancestor's depth is the length of the common prefix of the
-// two ancestor lists, kept as a bit mask during the walk.
+// GPU form.
+//   * One lane per sink, sinks in Morton order: the lanes of a warp are
+//     neighbours in space and visit almost the same cells.
+//   * Each lane runs a flat loop; one iteration is one walk step or one cell
+//     clip (the clips dominate: thousands per sink). The clip iteration picks
+//     its cell with selects from one per-lane list (sink ancestors | walk path
+//     | refinement stack), so lanes on different kinds of cells stay converged.
+//   * A warp owns a chunk of consecutive sinks; a lane that finishes its sink
+//     takes the next one of the chunk (ballot), so no lane idles while the
+//     warp's slowest sink finishes.
+//   * The segment cells of a ray are known without following parent links: the
+//     sibling of a cell is its index XOR 1 (children are allocated in pairs) and
+//     the common ancestor's depth is the length of the common prefix of the
+//     sink's ancestor list and the walk path, kept as a 64-bit mask.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,82 +37,11 @@ namespace trevr {
 
 namespace {
 
-constexpr int kDepth = 64;  // > max cell depth (63): stacks and ancestor lists never overflow
-
-struct Ray {
-  float px, py, pz;
-  float dx, dy, dz;
-  float ix, iy, iz;
-  float len;
-};
-
-// Length of the ray inside the box [a.xyz, b.xyz] (slab method, fp32); 0 if it misses.
-__device__ __forceinline__ float clip_len(const Ray& R, const float4& a, const float4& b) {
-  float t0 = 0.0f, t1 = 1.0f;
-  if (R.dx != 0.0f) {
-    float ta = __fmul_rn(__fsub_rn(a.x, R.px), R.ix);
-    float tb = __fmul_rn(__fsub_rn(b.x, R.px), R.ix);
-    t0 = fmaxf(t0, fminf(ta, tb));
-    t1 = fminf(t1, fmaxf(ta, tb));
-  } else if (R.px < a.x || R.px > b.x) {
-    return 0.0f;
-  }
-  if (R.dy != 0.0f) {
-    float ta = __fmul_rn(__fsub_rn(a.y, R.py), R.iy);
-    float tb = __fmul_rn(__fsub_rn(b.y, R.py), R.iy);
-    t0 = fmaxf(t0, fminf(ta, tb));
-    t1 = fminf(t1, fmaxf(ta, tb));
-  } else if (R.py < a.y || R.py > b.y) {
-    return 0.0f;
-  }
-  if (R.dz != 0.0f) {
-    float ta = __fmul_rn(__fsub_rn(a.z, R.pz), R.iz);
-    float tb = __fmul_rn(__fsub_rn(b.z, R.pz), R.iz);
-    t0 = fmaxf(t0, fminf(ta, tb));
-    t1 = fminf(t1, fmaxf(ta, tb));
-  } else if (R.pz < a.z || R.pz > b.z) {
-    return 0.0f;
-  }
-  return t1 > t0 ? __fmul_rn(__fsub_rn(t1, t0), R.len) : 0.0f;
-}
-
-// The same clip (identical length, so identical decisions) plus the gradient of the
-// length with respect to the ray's end point q. A slab parameter t = (b - p_k)/d_k
-// moves as dt/dq_k = -t/d_k; a parameter clamped to 0 or 1 does not move.
-__device__ __forceinline__ float clip_len_grad(const Ray& R, const float4& a, const float4& b,
-                                               float g[3]) {
-  float t0 = 0.0f, t1 = 1.0f;
-  int k0 = -1, k1 = -1;
-  const float pp[3] = {R.px, R.py, R.pz}, dd[3] = {R.dx, R.dy, R.dz}, ii[3] = {R.ix, R.iy, R.iz};
-  const float lo[3] = {a.x, a.y, a.z}, hi[3] = {b.x, b.y, b.z};
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    if (dd[k] != 0.0f) {
-      float ta = __fmul_rn(__fsub_rn(lo[k], pp[k]), ii[k]);
-      float tb = __fmul_rn(__fsub_rn(hi[k], pp[k]), ii[k]);
-      float tn = fminf(ta, tb), tx = fmaxf(ta, tb);
-      if (tn > t0) { t0 = tn; k0 = k; }
-      if (tx < t1) { t1 = tx; k1 = k; }
-    } else if (pp[k] < lo[k] || pp[k] > hi[k]) {
-      g[0] = g[1] = g[2] = 0.0f;
-      return 0.0f;
-    }
-  }
-  if (!(t1 > t0)) {
-    g[0] = g[1] = g[2] = 0.0f;
-    return 0.0f;
-  }
-  const float l = __fmul_rn(__fsub_rn(t1, t0), R.len);
-  const float w = (t1 - t0) / R.len;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    float dt = 0.0f;
-    if (k1 == k) dt -= t1 * ii[k];
-    if (k0 == k) dt += t0 * ii[k];
-    g[k] = dt * R.len + w * dd[k];
-  }
-  return l;
-}
+constexpr int kDepth = 64;  // > max cell depth (63): lists and stacks never overflow
+constexpr int kAnc = 0;     // offsets of the three parts of the per-lane list
+constexpr int kPath = kDepth;
+constexpr int kRef = 2 * kDepth;
+constexpr float kFourPi = 12.566370614359172f;
 
 // Neumaier-compensated fp32 sum.
 struct CSum {
@@ -120,6 +54,39 @@ struct CSum {
   }
   __device__ __forceinline__ float get() const { return __fadd_rn(s, c); }
 };
+
+// one slab of the clip: (lo - p) * (1/d), (hi - p) * (1/d), rounded after each step
+__device__ __forceinline__ void slab(float lo, float hi, float p, float d, float inv, float& t0,
+                                     float& t1, bool& miss) {
+  if (d != 0.0f) {
+    const float ta = __fmul_rn(__fsub_rn(lo, p), inv);
+    const float tb = __fmul_rn(__fsub_rn(hi, p), inv);
+    t0 = fmaxf(t0, fminf(ta, tb));
+    t1 = fminf(t1, fmaxf(ta, tb));
+  } else {
+    miss = miss || p < lo || p > hi;
+  }
+}
+
+// gradient-carrying slab: remembers which axis sets t0 / t1
+__device__ __forceinline__ void slab_g(int k, float lo, float hi, float p, float d, float inv,
+                                       float& t0, float& t1, int& k0, int& k1, bool& miss) {
+  if (d != 0.0f) {
+    const float ta = __fmul_rn(__fsub_rn(lo, p), inv);
+    const float tb = __fmul_rn(__fsub_rn(hi, p), inv);
+    const float tn = fminf(ta, tb), tx = fmaxf(ta, tb);
+    if (tn > t0) {
+      t0 = tn;
+      k0 = k;
+    }
+    if (tx < t1) {
+      t1 = tx;
+      k1 = k;
+    }
+  } else {
+    miss = miss || p < lo || p > hi;
+  }
+}
 
 }  // namespace
 
@@ -141,139 +108,150 @@ __device__ __forceinline__ void add_stats(const SinkCounters& c, unsigned long l
   }
 }
 
-// The whole hot path for one sink (sorted position i): the source walk, the
-// reverse rays with refinement and the flux sum; returns the flux (forward) or
-// scatters the adjoint contributions for dLoss/dF = gk (ADJ).
-template <bool ADJ>
-__device__ __forceinline__ float walk_sink(const TreeView& T, const int i, const float gk,
-                                           const WalkParams& P, int* status,
-                                           const AdjointArgs& J, SinkCounters& cnt) {
-  const float4 p = T.pos[i];
-  const int S = T.leaf_of[i];
-  const int dS = __ldg(&T.ndepth[S]);
-  const int stack_limit = P.stack_depth < kDepth ? P.stack_depth : kDepth;
+// Per-lane lists, kept apart from the scalar state so that the state stays in
+// registers: the ancestors of S | the depth-first path | cells to clip, and the
+// walk stack (cell, depth).
+struct Lists {
+  int lst[3 * kDepth];
+  int wstack[kDepth];
+  int wdepth[kDepth];
+};
 
-  int anc[kDepth];     // ancestors of S by depth (anc[dS] = S)
-  int path[kDepth];    // current depth-first path of the walk
-  int wstack[kDepth];  // walk stack: cell index
-  int wdepth[kDepth];  //             and its depth
-  int rstack[kDepth];  // cells waiting to be clipped (refinement)
-  {
+// State of one lane: the sink it works on, its walk and its current ray.
+// ADJ = false computes the flux. ADJ = true is the adjoint with the same
+// decisions: every ray is traced twice, first for tau and d(tau)/dq, then, with
+// the contribution f known, to scatter -g f l_X into each segment cell.
+template <bool ADJ>
+struct Lane {
+  // sink
+  int i;     // sorted position
+  float gk;  // dLoss/dF of this sink (adjoint)
+  float px, py, pz;
+  int S, dS;
+  unsigned long long on_path;  // bit d: path[d] is an ancestor of S
+  int sp;                      // walk stack size
+  CSum F;
+  SinkCounters cnt;  // this sink's counters
+  // ray
+  bool in_ray;
+  float dx, dy, dz, ix, iy, iz, len, s2, rayL;
+  CSum tau;
+  int C, dC, nSs, nb, b, rsp, boxes;
+  // single sources of an opened leaf
+  int j, j_end, leafC, dleaf;
+  // adjoint
+  int pass, src_j;
+  float gq0, gq1, gq2, fcur;
+  __device__ __forceinline__ void begin(const TreeView& T, int i_, float g, Lists& L_) {
+    int* lst = L_.lst;
+    int* wstack = L_.wstack;
+    int* wdepth = L_.wdepth;
+    i = i_;
+    gk = g;
+    const float4 p = T.pos[i];
+    px = p.x;
+    py = p.y;
+    pz = p.z;
+    S = T.leaf_of[i];
+    dS = __ldg(&T.ndepth[S]);
     int u = S;
     for (int d = dS; d >= 0; --d) {
-      anc[d] = u;
+      lst[kAnc + d] = u;
       u = __ldg(&T.nT[u].y);
     }
+    on_path = 0;
+    wstack[0] = kRoot;
+    wdepth[0] = 0;
+    sp = 1;
+    F = CSum();
+    cnt = SinkCounters();
+    in_ray = false;
+    j = j_end = 0;
   }
-  unsigned long long on_path = 0;  // bit d: path[d] is an ancestor of S (or S)
-  wstack[0] = kRoot;
-  wdepth[0] = 0;
-  int sp = 1;
 
-  CSum F;
-  // ray state
-  bool in_ray = false;
-  Ray R;
-  R.px = p.x;
-  R.py = p.y;
-  R.pz = p.z;
-  CSum tau;
-  float rayL = 0.0f, s2 = 0.0f;
-  int C = 0, dC = 0, dstar = 0, nb = 0, b = 0, rsp = 0;
-  // single sources of an opened leaf
-  int j = 0, j_end = 0, leafC = 0, dleaf = 0;
-  const int box_limit = 2 * T.n_nodes_cap + 4;
-  int boxes = 0;
-  // adjoint state
-  int pass = 1, src_j = -1;
-  float gq0 = 0.0f, gq1 = 0.0f, gq2 = 0.0f, fcur = 0.0f;
-
-  while (true) {
+  // One iteration. Returns false when the sink is finished.
+  __device__ __forceinline__ bool step(const TreeView& T, const WalkParams& P, int stack_limit,
+                                       int box_limit, int* status, const AdjointArgs& J,
+                                       Lists& L_) {
+    int* lst = L_.lst;
+    int* wstack = L_.wstack;
+    int* wdepth = L_.wdepth;
     if (in_ray) {
-      int box;
-      if (rsp > 0) {
-        box = rstack[--rsp];
-      } else if (b < nb) {
-        const int nS_side = dS - dstar - 1;  // siblings on the sink side
-        if (b == 0) box = S;
-        else if (b <= nS_side) box = anc[dS - b + 1] ^ 1;
-        else if (b == nS_side + 1) box = C;
-        else box = path[dC - (b - nS_side - 2)] ^ 1;
-        ++b;
-      } else {
-        const float t = tau.get();
-        const float f = rayL * expf(-t) / (12.566370614359172f * s2);
-        if (!ADJ) {
-          F.add(f);
-          ++cnt.rays;
-          in_ray = false;
-        } else if (pass == 1) {
-          // second pass over the same cells, now that f is known
-          fcur = f;
-          pass = 2;
-          b = 0;
-          rsp = 0;
-          boxes = 0;
-        } else {
-          const float gf = gk * fcur;
-          if (src_j >= 0) {
-            atomicAdd(&J.e[src_j], (double)(gf / rayL));
-          } else {
-            const float c = gf / rayL, inv_s2 = 2.0f / s2;
-            atomicAdd(&J.a[C], (double)c);
-            atomicAdd(&J.b[3 * C + 0], (double)(c * (-R.dx * inv_s2 - gq0)));
-            atomicAdd(&J.b[3 * C + 1], (double)(c * (-R.dy * inv_s2 - gq1)));
-            atomicAdd(&J.b[3 * C + 2], (double)(c * (-R.dz * inv_s2 - gq2)));
-          }
-          ++cnt.rays;
-          in_ray = false;
-        }
-        continue;
+      const bool from_stack = rsp > 0;
+      if (!from_stack && b >= nb) {
+        finish_ray(J);
+        return true;
       }
+      // the next cell, by selects: refinement stack, else S, sink-side siblings,
+      // C, pseudo-source-side siblings
+      int off = kRef + rsp - 1;
+      if (!from_stack) off = (b <= nSs) ? (kAnc + dS - b + 1) : (kPath + dC - (b - nSs - 2));
+      const int v = lst[off];
+      const int box = from_stack ? v : ((b == 0) ? S : ((b == nSs + 1) ? C : (v ^ 1)));
+      rsp -= from_stack ? 1 : 0;
+      b += from_stack ? 0 : 1;
       if (++boxes > box_limit) {
         atomicOr(status, kStatusIterationLimit);
-        break;
+        return false;
       }
       const float4 a = __ldg(&T.nA[box]);
       const float4 bb = __ldg(&T.nB[box]);
-      float gl[3];
       const bool want_grad = ADJ && pass == 1 && src_j < 0;
-      const float l = want_grad ? clip_len_grad(R, a, bb, gl) : clip_len(R, a, bb);
+      float t0 = 0.0f, t1 = 1.0f;
+      bool miss = false;
+      int k0 = -1, k1 = -1;
+      if (want_grad) {
+        slab_g(0, a.x, bb.x, px, dx, ix, t0, t1, k0, k1, miss);
+        slab_g(1, a.y, bb.y, py, dy, iy, t0, t1, k0, k1, miss);
+        slab_g(2, a.z, bb.z, pz, dz, iz, t0, t1, k0, k1, miss);
+      } else {
+        slab(a.x, bb.x, px, dx, ix, t0, t1, miss);
+        slab(a.y, bb.y, py, dy, iy, t0, t1, miss);
+        slab(a.z, bb.z, pz, dz, iz, t0, t1, miss);
+      }
+      const float l = (!miss && t1 > t0) ? __fmul_rn(__fsub_rn(t1, t0), len) : 0.0f;
       ++cnt.clip;
-      if (!(l > 0.0f)) continue;
+      if (!(l > 0.0f)) return true;
       if (P.tau_ref <= 0.0f || __fmul_rn(bb.w, l) > P.tau_ref) {
         const int child = __ldg(&T.nT[box].x);
         if (child >= 0) {
           if (rsp + 2 > stack_limit) {
             atomicOr(status, kStatusStackOverflow);
-            break;
+            return false;
           }
           ++cnt.ref;
-          rstack[rsp++] = child + 1;
-          rstack[rsp++] = child;
-          continue;
+          lst[kRef + rsp] = child + 1;
+          lst[kRef + rsp + 1] = child;
+          rsp += 2;
+          return true;
         }
       }
       if (ADJ && pass == 2) {
         atomicAdd(&J.G[box], (double)(-gk * fcur * l));
-        continue;
+        return true;
       }
       tau.add(a.w * l);
       if (want_grad) {
-        gq0 = fmaf(a.w, gl[0], gq0);
-        gq1 = fmaf(a.w, gl[1], gq1);
-        gq2 = fmaf(a.w, gl[2], gq2);
+        // d l / d q: a slab parameter t = (b - p_k)/d_k moves as -t/d_k along q_k;
+        // one clamped to 0 or 1 does not move
+        const float w = (t1 - t0) / len;
+        const float g0 = (k1 == 0 ? -t1 * ix : 0.0f) + (k0 == 0 ? t0 * ix : 0.0f);
+        const float g1 = (k1 == 1 ? -t1 * iy : 0.0f) + (k0 == 1 ? t0 * iy : 0.0f);
+        const float g2 = (k1 == 2 ? -t1 * iz : 0.0f) + (k0 == 2 ? t0 * iz : 0.0f);
+        gq0 = fmaf(a.w, g0 * len + w * dx, gq0);
+        gq1 = fmaf(a.w, g1 * len + w * dy, gq1);
+        gq2 = fmaf(a.w, g2 * len + w * dz, gq2);
       }
       ++cnt.segs;
-      continue;
+      return true;
     }
 
-    // ---- walk step: next pseudo-source
+    // ---- walk step: find the next pseudo-source
     float qx, qy, qz, L;
     if (j < j_end) {
       const float4 y = __ldg(&T.src[j]);
       ++j;
-      if (!(y.w > 0.0f)) continue;
+      if (!(y.w > 0.0f)) return true;
       C = leafC;
       dC = dleaf;
       src_j = j - 1;
@@ -282,21 +260,21 @@ __device__ __forceinline__ float walk_sink(const TreeView& T, const int i, const
       qz = y.z;
       L = y.w;
     } else {
-      if (sp == 0) break;
+      if (sp == 0) return false;  // the sink is done
       --sp;
       const int X = wstack[sp];
       const int dX = wdepth[sp];
-      path[dX] = X;
+      lst[kPath + dX] = X;
       const unsigned long long bit = 1ull << dX;
-      on_path = (dX <= dS && anc[dX] == X) ? (on_path | bit) : (on_path & ~bit);
+      on_path = (dX <= dS && lst[kAnc + dX] == X) ? (on_path | bit) : (on_path & ~bit);
       const float4 s = __ldg(&T.nS[X]);
-      if (!(s.w > 0.0f)) continue;
+      if (!(s.w > 0.0f)) return true;
       ++cnt.visit;
       const float4 a = __ldg(&T.nA[X]);
       const float4 bb = __ldg(&T.nB[X]);
-      const float ex = fmaxf(fmaxf(__fsub_rn(a.x, p.x), __fsub_rn(p.x, bb.x)), 0.0f);
-      const float ey = fmaxf(fmaxf(__fsub_rn(a.y, p.y), __fsub_rn(p.y, bb.y)), 0.0f);
-      const float ez = fmaxf(fmaxf(__fsub_rn(a.z, p.z), __fsub_rn(p.z, bb.z)), 0.0f);
+      const float ex = fmaxf(fmaxf(__fsub_rn(a.x, px), __fsub_rn(px, bb.x)), 0.0f);
+      const float ey = fmaxf(fmaxf(__fsub_rn(a.y, py), __fsub_rn(py, bb.y)), 0.0f);
+      const float ez = fmaxf(fmaxf(__fsub_rn(a.z, pz), __fsub_rn(pz, bb.z)), 0.0f);
       const float r2 =
           __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
       if (!(__ldg(&T.nl2[X]) < __fmul_rn(P.theta2, r2))) {
@@ -309,7 +287,7 @@ __device__ __forceinline__ float walk_sink(const TreeView& T, const int i, const
         } else {
           if (sp + 2 > stack_limit) {
             atomicOr(status, kStatusStackOverflow);
-            break;
+            return false;
           }
           wstack[sp] = t.x + 1;
           wdepth[sp] = dX + 1;
@@ -317,7 +295,7 @@ __device__ __forceinline__ float walk_sink(const TreeView& T, const int i, const
           wdepth[sp + 1] = dX + 1;
           sp += 2;
         }
-        continue;
+        return true;
       }
       C = X;
       dC = dX;
@@ -328,16 +306,15 @@ __device__ __forceinline__ float walk_sink(const TreeView& T, const int i, const
       L = s.w;
     }
     // ---- start the reverse ray from the sink to (q, L) in cell C
-    R.dx = __fsub_rn(qx, p.x);
-    R.dy = __fsub_rn(qy, p.y);
-    R.dz = __fsub_rn(qz, p.z);
-    s2 = __fadd_rn(__fadd_rn(__fmul_rn(R.dx, R.dx), __fmul_rn(R.dy, R.dy)),
-                   __fmul_rn(R.dz, R.dz));
-    if (s2 < P.smin2) continue;  // a source on top of the sink adds nothing
-    R.len = __fsqrt_rn(s2);
-    R.ix = R.dx != 0.0f ? __frcp_rn(R.dx) : 0.0f;
-    R.iy = R.dy != 0.0f ? __frcp_rn(R.dy) : 0.0f;
-    R.iz = R.dz != 0.0f ? __frcp_rn(R.dz) : 0.0f;
+    dx = __fsub_rn(qx, px);
+    dy = __fsub_rn(qy, py);
+    dz = __fsub_rn(qz, pz);
+    s2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    if (s2 < P.smin2) return true;  // a source on top of the sink adds nothing
+    len = __fsqrt_rn(s2);
+    ix = dx != 0.0f ? __frcp_rn(dx) : 0.0f;
+    iy = dy != 0.0f ? __frcp_rn(dy) : 0.0f;
+    iz = dz != 0.0f ? __frcp_rn(dz) : 0.0f;
     rayL = L;
     tau = CSum();
     pass = 1;
@@ -346,63 +323,176 @@ __device__ __forceinline__ float walk_sink(const TreeView& T, const int i, const
     rsp = 0;
     boxes = 0;
     if (C == S) {
+      nSs = 0;
       nb = 1;
     } else {
       // depth of the lowest common ancestor: the common prefix of path and anc
       const int mn = dC < dS ? dC : dS;
       const unsigned long long m = on_path & ((2ull << mn) - 1ull);  // mn <= 62
-      dstar = __ffsll((long long)~m) - 2;
+      const int dstar = __ffsll((long long)~m) - 2;
+      nSs = dS - dstar - 1;  // siblings on the sink side
       nb = dS + dC - 2 * dstar;
     }
     in_ray = true;
+    return true;
   }
-  return F.get();
+
+  __device__ __forceinline__ void finish_ray(const AdjointArgs& J) {
+    const float t = tau.get();
+    const float f = rayL * expf(-t) / (kFourPi * s2);
+    if (!ADJ) {
+      F.add(f);
+      ++cnt.rays;
+      in_ray = false;
+    } else if (pass == 1) {
+      // second pass over the same cells, now that f is known
+      fcur = f;
+      pass = 2;
+      b = 0;
+      rsp = 0;
+      boxes = 0;
+    } else {
+      const float gf = gk * fcur;
+      if (src_j >= 0) {
+        atomicAdd(&J.e[src_j], (double)(gf / rayL));
+      } else {
+        const float c = gf / rayL, inv_s2 = 2.0f / s2;
+        atomicAdd(&J.a[C], (double)c);
+        atomicAdd(&J.b[3 * C + 0], (double)(c * (-dx * inv_s2 - gq0)));
+        atomicAdd(&J.b[3 * C + 1], (double)(c * (-dy * inv_s2 - gq1)));
+        atomicAdd(&J.b[3 * C + 2], (double)(c * (-dz * inv_s2 - gq2)));
+      }
+      ++cnt.rays;
+      in_ray = false;
+    }
+  }
+};
+
+// Where a finished sink's results go.
+struct SinkOut {
+  float* flux;    // flux per sink (caller order), or nullptr
+  int* counters;  // 4 int per sink, or nullptr
+};
+
+// Runs the sinks [first, end) of a chunk with one warp: the lanes start on the
+// first 32 and take the next unclaimed sink of the chunk when theirs is done.
+// `map` turns a chunk position into (sorted position, output slot, dLoss/dF);
+// positions it rejects are skipped. Every lane of the warp must call it.
+template <bool ADJ, class Map>
+__device__ __forceinline__ void run_chunk(const TreeView& T, const WalkParams& P, int first,
+                                          int end, const Map& map, const SinkOut& out,
+                                          int* status, const AdjointArgs& J, SinkCounters& tot) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned lt = (1u << lane) - 1u;
+  const int stack_limit = P.stack_depth < kDepth ? P.stack_depth : kDepth;
+  const int box_limit = 2 * T.n_nodes_cap + 4;
+  Lane<ADJ> st;
+  Lists lists;
+  int next = first;     // next unclaimed chunk position (same value in every lane)
+  bool active = false;  // this lane holds a sink
+  int slot = -1;        // output slot of the lane's sink
+  while (true) {
+    // idle lanes claim the next positions of the chunk, in lane order
+    const unsigned idle = __ballot_sync(0xffffffffu, !active);
+    if (idle) {
+      if (next >= end) {
+        if (idle == 0xffffffffu) break;
+      } else {
+        const int pos = next + (int)__popc(idle & lt);
+        if (!active && pos < end) {
+          int i;
+          float g;
+          if (map(pos, i, slot, g)) {
+            st.begin(T, i, g, lists);
+            active = true;
+          }
+        }
+        next += (int)__popc(idle);
+        continue;  // a lane whose position was rejected claims again next round
+      }
+    }
+    if (active && !st.step(T, P, stack_limit, box_limit, status, J, lists)) {
+      active = false;
+      if (!ADJ) {
+        if (out.flux) out.flux[slot] = st.F.get();
+        if (out.counters)
+          reinterpret_cast<int4*>(out.counters)[slot] =
+              make_int4(st.cnt.rays, st.cnt.segs, st.cnt.visit, st.cnt.ref);
+      }
+      tot.rays += st.cnt.rays;
+      tot.segs += st.cnt.segs;
+      tot.visit += st.cnt.visit;
+      tot.ref += st.cnt.ref;
+      tot.clip += st.cnt.clip;
+    }
+  }
 }
 
-// ADJ = false: forward flux. ADJ = true: the adjoint with the same decisions; every
-// ray is traced twice, first for tau and d(tau)/dq, then, with the contribution f
-// known, to scatter -g f l_X into each segment cell (FP64 atomics).
+// Sinks of a plain call: chunk position k is the k-th requested sink.
 template <bool ADJ>
-__global__ void __launch_bounds__(128) walk_flat_kernel(TreeView T, const long long* sink_idx,
-                                                        int n_sink, WalkParams P, float* flux_out,
-                                                        int* counters,
-                                                        unsigned long long* stats, int* status,
-                                                        AdjointArgs J) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  SinkCounters cnt;
-  bool valid = k < n_sink;
-  if (valid && sink_idx) {
-    const long long si = sink_idx[k];
-    if (si < 0 || si >= T.n_gas) {
-      atomicOr(status, kStatusInvalid);
-      if (!ADJ) flux_out[k] = 0.0f;
-      if (counters) reinterpret_cast<int4*>(counters)[k] = make_int4(0, 0, 0, 0);
-      valid = false;
+struct PlainMap {
+  const TreeView* T;
+  const long long* sink_idx;
+  const float* grad_flux;
+  int* status;
+  __device__ __forceinline__ bool operator()(int k, int& i, int& slot, float& g) const {
+    if (sink_idx) {
+      const long long si = sink_idx[k];
+      if (si < 0 || si >= T->n_gas) {
+        atomicOr(status, kStatusInvalid);
+        return false;
+      }
+      i = T->rank[si];
+      slot = k;
+    } else {
+      i = k;
+      slot = T->perm[k];
     }
+    g = ADJ ? grad_flux[slot] : 0.0f;
+    return !ADJ || g != 0.0f;  // the adjoint skips sinks with dLoss/dF = 0
   }
-  if (ADJ && valid) {
-    // the adjoint skips sinks whose dLoss/dF (caller order, like the fluxes) is zero
-    const int i0 = sink_idx ? T.rank[sink_idx[k]] : k;
-    if (J.grad_flux[sink_idx ? k : T.perm[i0]] == 0.0f) valid = false;
-  }
-  if (valid) {
-    const int i = sink_idx ? T.rank[sink_idx[k]] : k;
-    const float gk = ADJ ? J.grad_flux[sink_idx ? k : T.perm[i]] : 0.0f;
-    const float Fv = walk_sink<ADJ>(T, i, gk, P, status, J, cnt);
-    if (!ADJ) {
-      const int out = sink_idx ? k : T.perm[i];
-      flux_out[out] = Fv;
-      if (counters)
-        reinterpret_cast<int4*>(counters)[out] = make_int4(cnt.rays, cnt.segs, cnt.visit, cnt.ref);
+};
+
+template <bool ADJ>
+__global__ void __launch_bounds__(128) walk_kernel(TreeView T, const long long* sink_idx,
+                                                   int n_sink, int chunk, WalkParams P,
+                                                   SinkOut out, unsigned long long* stats,
+                                                   int* status, AdjointArgs J) {
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long first = warp * chunk;
+  SinkCounters tot;
+  if (first < n_sink) {
+    const int end = (int)min((long long)n_sink, first + chunk);
+    if (!ADJ && sink_idx) {  // sinks with an index out of range get zeros
+      for (int k = (int)first + (int)(threadIdx.x & 31); k < end; k += 32) {
+        const long long si = sink_idx[k];
+        if (si < 0 || si >= T.n_gas) {
+          if (out.flux) out.flux[k] = 0.0f;
+          if (out.counters) reinterpret_cast<int4*>(out.counters)[k] = make_int4(0, 0, 0, 0);
+        }
+      }
     }
+    PlainMap<ADJ> map{&T, sink_idx, J.grad_flux, status};
+    run_chunk<ADJ>(T, P, (int)first, end, map, out, status, J, tot);
   }
-  if (stats) add_stats(cnt, stats);
+  if (stats) add_stats(tot, stats);
 }
+
+// Batched form: sorted positions of one tree, output in that tree's caller order.
+struct TreeMap {
+  const TreeView* T;
+  __device__ __forceinline__ bool operator()(int k, int& i, int& slot, float& g) const {
+    i = k;
+    slot = T->perm[k];
+    g = 0.0f;
+    return true;
+  }
+};
 
 // Many independent trees in one persistent launch. Work items are runs of
 // `item` consecutive sinks (Morton order) of one tree; each warp takes the next
 // item from a device counter, so warps that finish early keep pulling work from
-// the boxes that are left. Per-sink arithmetic is the same as walk_flat_kernel.
+// the boxes that are left. Per-sink arithmetic is the same as walk_kernel.
 template <int BS>
 __global__ void __launch_bounds__(BS) walk_batched_kernel(const TreeView* __restrict__ views,
                                                          float* const* __restrict__ flux_out,
@@ -411,7 +501,7 @@ __global__ void __launch_bounds__(BS) walk_batched_kernel(const TreeView* __rest
                                                          unsigned* counter, WalkParams P,
                                                          unsigned long long* stats, int* status) {
   const unsigned lane = threadIdx.x & 31u;
-  SinkCounters cnt;
+  SinkCounters tot;
   while (true) {
     unsigned it = 0;
     if (lane == 0) it = atomicAdd(counter, 1u);
@@ -419,17 +509,14 @@ __global__ void __launch_bounds__(BS) walk_batched_kernel(const TreeView* __rest
     if (it >= (unsigned)n_items) break;
     const int2 w = items[it];
     const TreeView T = views[w.x];
-    float* out = flux_out[w.x];
     WalkParams Pt = P;  // the coincident-source cut (1e-12 side)^2 of this tree, in fp32
     const float smin = __fmul_rn(1e-12f, T.side);
     Pt.smin2 = __fmul_rn(smin, smin);
-    const int end = min(w.y + item, T.n_gas);
-    for (int i = w.y + (int)lane; i < end; i += 32) {
-      const float f = walk_sink<false>(T, i, 0.0f, Pt, status, AdjointArgs{}, cnt);
-      out[T.perm[i]] = f;
-    }
+    SinkOut out{flux_out[w.x], nullptr};
+    TreeMap map{&T};
+    run_chunk<false>(T, Pt, w.y, min(w.y + item, T.n_gas), map, out, status, AdjointArgs{}, tot);
   }
-  if (stats) add_stats(cnt, stats);
+  if (stats) add_stats(tot, stats);
 }
 
 cudaError_t launch_walk_batched(const TreeView* views, float* const* flux_out, const int2* items,
@@ -457,16 +544,22 @@ cudaError_t launch_walk_batched(const TreeView* views, float* const* flux_out, c
   return cudaGetLastError();
 }
 
+static int chunk_of(const WalkParams& wp) {
+  return wp.sinks_per_warp > 0 ? wp.sinks_per_warp : kDefaultChunk;
+}
+
 cudaError_t launch_walk(const TreeView& T, const long long* sink_idx, int n_sink,
                         const WalkParams& wp, float* flux_out, int* counters,
                         unsigned long long* stats, int* status, int block_size,
                         cudaStream_t s) {
   if (n_sink <= 0) return cudaSuccess;
-  const int threads = 128;
   (void)block_size;
-  const int blocks = (n_sink + threads - 1) / threads;
-  walk_flat_kernel<false><<<blocks, threads, 0, s>>>(T, sink_idx, n_sink, wp, flux_out, counters,
-                                                     stats, status, AdjointArgs{});
+  const int chunk = chunk_of(wp);
+  const long long warps = ((long long)n_sink + chunk - 1) / chunk;
+  const int blocks = (int)((warps * 32 + 127) / 128);
+  walk_kernel<false><<<blocks, 128, 0, s>>>(T, sink_idx, n_sink, chunk, wp,
+                                            SinkOut{flux_out, counters}, stats, status,
+                                            AdjointArgs{});
   note_launch();
   return cudaGetLastError();
 }
@@ -475,10 +568,11 @@ cudaError_t launch_walk_adjoint(const TreeView& T, const long long* sink_idx, in
                                 const WalkParams& wp, const AdjointArgs& J, int* status,
                                 cudaStream_t s) {
   if (n_sink <= 0) return cudaSuccess;
-  const int threads = 128;
-  const int blocks = (n_sink + threads - 1) / threads;
-  walk_flat_kernel<true><<<blocks, threads, 0, s>>>(T, sink_idx, n_sink, wp, nullptr, nullptr,
-                                                    nullptr, status, J);
+  const int chunk = chunk_of(wp);
+  const long long warps = ((long long)n_sink + chunk - 1) / chunk;
+  const int blocks = (int)((warps * 32 + 127) / 128);
+  walk_kernel<true><<<blocks, 128, 0, s>>>(T, sink_idx, n_sink, chunk, wp,
+                                           SinkOut{nullptr, nullptr}, nullptr, status, J);
   note_launch();
   return cudaGetLastError();
 }
