@@ -56,6 +56,22 @@ def _config(P, name, desc):
             "l2": "flushed between timed steps (256 MiB write)"}
 
 
+def reduce_max(value, world, device):
+    """Max of a per-rank scalar over all ranks (the step time of the slowest rank)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, t_ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / (t_ms * 1e-3)
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -215,7 +231,8 @@ def _bench_batched(args):
     th, tr = boxes[0]["theta"], boxes[0]["tau_ref"]
     B = trevr.Batch(trees)
     tune = autotune.tune(B, th, tr)
-    shape = dict(sinks_per_warp=tune["sinks_per_warp"], block_size=tune["block_size"])
+    shape = dict(sinks_per_warp=tune["sinks_per_warp"], block_size=tune["block_size"],
+                 walk_variant=tune.get("walk_variant", 0))
     B.capture(th, tr, **shape)
     for _ in range(args.warmup):
         B.replay()
@@ -326,13 +343,10 @@ def run_ours(args):
     step_ms = [e[0].elapsed_time(e[2]) for e in evs]
     build_ms = [e[0].elapsed_time(e[1]) for e in evs]
     walk_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    t_step = sum(step_ms) / len(step_ms)
+    t_step = reduce_max(sum(step_ms) / len(step_ms), world, dev)
     if world > 1:
-        tt = torch.tensor([t_step], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(tt.item())
         torch.distributed.barrier()
-    value = world * n / (t_step * 1e-3)
+    value = job_value(n, world, t_step)
 
     # end to end through the public API with host buffers: pinned H2D of the
     # step's inputs, build, flux, D2H of the fluxes, all inside the timed region
@@ -365,11 +379,7 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    t_e2e = sum(e2e_ms) / len(e2e_ms)
-    if world > 1:
-        tt = torch.tensor([t_e2e], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+    t_e2e = reduce_max(sum(e2e_ms) / len(e2e_ms), world, dev)
 
     if rank != 0:
         if world > 1:
@@ -384,7 +394,7 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     achieved = alg_bytes / t_walk / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "walk_kernel<false> (sink walk + rays + flux)",
+                "frac": achieved / peak, "traffic": None, "kernel": "walk_warp_kernel<false> (warp-shared sink walk + rays + flux)",
                 "peak_kind": f"{peak_kind} (copy bandwidth, burst)",
                 "bytes_per_launch": alg_bytes}
 
@@ -400,7 +410,7 @@ def run_ours(args):
                          "refinements": st["refine_expansions"] / n,
                          "cells_clipped": st["cells_clipped"] / n},
             "roofline": roofline,
-            "e2e": {"value": world * n / (t_e2e * 1e-3), "unit": UNIT,
+            "e2e": {"value": job_value(n, world, t_e2e), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "clocks": clk}
 

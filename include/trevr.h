@@ -64,6 +64,9 @@ typedef struct {
                            its sink takes the next of the chunk); 0 = default (32) */
     int block_size;     /* threads per block of the walk, 0 = default */
     int stack_depth;    /* traversal stack entries per sink, 0 = default (64) */
+    int walk_variant;   /* 1 = every lane walks its own sink; 2 = the 32 lanes of a warp
+                           walk one shared stack and trace together the rays to a cell
+                           they accept together; 0 = default (2) */
 } trevr_params;
 
 /* Totals over the sinks of one call, and timings (ms, CUDA events). */

@@ -39,6 +39,7 @@ static WalkParams walk_params(const trevr_tree* t, const trevr_params* prm) {
   wp.smin2 = smin * smin;
   wp.stack_depth = prm->stack_depth > 0 ? prm->stack_depth : kDefaultStack;
   wp.sinks_per_warp = prm->sinks_per_warp;
+  wp.variant = prm->walk_variant > 0 ? prm->walk_variant : kDefaultVariant;
   return wp;
 }
 
@@ -49,6 +50,7 @@ static bool params_ok(const trevr_params* prm) {
   if (prm->stack_depth < 0 || prm->stack_depth > kMaxStack) return false;
   if (prm->block_size < 0 || prm->block_size > 1024 || (prm->block_size % 32) != 0) return false;
   if (prm->sinks_per_warp < 0) return false;
+  if (prm->walk_variant < 0 || prm->walk_variant > 2) return false;
   return true;
 }
 
@@ -274,6 +276,7 @@ int trevr_compute_flux_batched(trevr_batch* B, const trevr_params* prm, float* c
   wp.stack_depth = prm->stack_depth > 0 ? prm->stack_depth : kDefaultStack;
   wp.smin2 = 0.0f;  // set per tree by the kernel from the tree's side
   wp.sinks_per_warp = item;
+  wp.variant = prm->walk_variant > 0 ? prm->walk_variant : kDefaultVariant;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));

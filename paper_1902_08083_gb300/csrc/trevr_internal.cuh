@@ -19,6 +19,7 @@ constexpr int kMaxLevels = 66;            // depth <= 63 (one key bit per cut), 
 constexpr int kDefaultStack = 64;         // >= max depth + 1: a walk can never overflow it
 constexpr int kMaxStack = 128;
 constexpr int kDefaultChunk = 32;         // sinks per warp of the walk (one per lane)
+constexpr int kDefaultVariant = 2;        // walk variant used when the caller passes 0
 
 // device status bits (OR-ed by kernels, mapped to TREVR_ERR_* on the host)
 constexpr int kStatusOutOfDomain = 1;
@@ -138,6 +139,7 @@ struct WalkParams {
   float smin2;   // (1e-12 side)^2 (fp32): coincident-source cut
   int stack_depth;
   int sinks_per_warp;  // sinks in each warp's chunk (0 = default)
+  int variant;         // 1 = per-lane walk, 2 = warp-shared walk
 };
 // accumulators of the adjoint (FP64, zeroed by the caller)
 struct AdjointArgs {

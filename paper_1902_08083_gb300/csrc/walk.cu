@@ -519,6 +519,358 @@ __global__ void __launch_bounds__(BS) walk_batched_kernel(const TreeView* __rest
   if (stats) add_stats(tot, stats);
 }
 
+// ---------------------------------------------------------------------------
+// Warp-shared walk (variant 2). The 32 lanes of a warp (32 consecutive sinks in
+// Morton order) walk ONE depth-first stack held in shared memory; each entry
+// carries the mask of lanes that still need the cell. A cell that several
+// lanes accept is traced by all of them at once, to the same pseudo-source, so
+// the cells on the pseudo-source's side and the shared part of the sinks' side
+// are the same addresses in every lane (one broadcast load). The segment order
+// is chosen for that: C, then C's side from deep to shallow, then the sink's
+// side from shallow to deep, then S.
+// ---------------------------------------------------------------------------
+struct WarpStack {
+  int node[kDepth + 2];
+  int depth[kDepth + 2];
+  unsigned mask[kDepth + 2];
+  int path[kDepth];  // the walk's depth-first path
+};
+
+// Sum of v over the lanes that asked (key >= 0) when they all name the same cell,
+// else one atomic per lane. Every lane of the warp must call it.
+__device__ __forceinline__ void warp_atomic_add(double* base, int key, float v) {
+  const unsigned FULL = 0xffffffffu;
+  const unsigned want = __ballot_sync(FULL, key >= 0);
+  if (!want) return;
+  const int k0 = __shfl_sync(FULL, key, __ffs(want) - 1);
+  if (__all_sync(FULL, key < 0 || key == k0)) {
+    float x = key >= 0 ? v : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&base[k0], (double)x);
+  } else if (key >= 0) {
+    atomicAdd(&base[key], (double)v);
+  }
+}
+
+// Rays from the sinks of the lanes in `on` to (q, L) inside cell C; every lane
+// of the warp must call it (the loop runs while any lane has cells left).
+template <bool ADJ>
+__device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P, const bool on,
+                                         const float px, const float py, const float pz,
+                                         const int S, const int dS, const int* anc, int* rst,
+                                         const unsigned long long on_path, const int* path,
+                                         const int C, const int dC, const float qx,
+                                         const float qy, const float qz, const float L,
+                                         const int src_j, const float gk, const int stack_limit,
+                                         const int box_limit, int* status, const AdjointArgs& J,
+                                         SinkCounters& cnt, CSum& F) {
+  const unsigned FULL = 0xffffffffu;
+  float dx = 0.0f, dy = 0.0f, dz = 0.0f, s2 = 1.0f, len = 1.0f, ix = 0.0f, iy = 0.0f, iz = 0.0f;
+  int nCs = 0, nSs = 0, nb = 0, dstar = 0;
+  bool active = false;
+  if (on) {
+    dx = __fsub_rn(qx, px);
+    dy = __fsub_rn(qy, py);
+    dz = __fsub_rn(qz, pz);
+    s2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    if (!(s2 < P.smin2)) {  // a source on top of the sink adds nothing
+      active = true;
+      len = __fsqrt_rn(s2);
+      ix = dx != 0.0f ? __frcp_rn(dx) : 0.0f;
+      iy = dy != 0.0f ? __frcp_rn(dy) : 0.0f;
+      iz = dz != 0.0f ? __frcp_rn(dz) : 0.0f;
+      if (C == S) {
+        nb = 1;
+      } else {
+        const int mn = dC < dS ? dC : dS;
+        const unsigned long long m = on_path & ((2ull << mn) - 1ull);  // mn <= 62
+        dstar = __ffsll((long long)~m) - 2;
+        nCs = dC - dstar - 1;
+        nSs = dS - dstar - 1;
+        nb = nCs + nSs + 2;
+      }
+    }
+  }
+  const bool traced = active;
+  CSum tau;
+  int b = 0, rsp = 0, boxes = 0, pass = 1;
+  float gq0 = 0.0f, gq1 = 0.0f, gq2 = 0.0f, fcur = 0.0f;
+  while (__any_sync(FULL, active)) {
+    int akey = -1;
+    float aval = 0.0f;
+    if (active) {
+      const bool from_stack = rsp > 0;
+      if (!from_stack && b >= nb) {
+        const float f = L * expf(-tau.get()) / (kFourPi * s2);
+        if (!ADJ) {
+          F.add(f);
+          ++cnt.rays;
+          active = false;
+        } else if (pass == 1) {
+          fcur = f;  // second pass over the same cells, now that f is known
+          pass = 2;
+          b = 0;
+          rsp = 0;
+          boxes = 0;
+        } else {
+          ++cnt.rays;
+          active = false;
+        }
+      } else {
+        int box;
+        if (from_stack) {
+          box = rst[--rsp];
+        } else {
+          if (nb == 1) box = S;
+          else if (b == 0) box = C;
+          else if (b <= nCs) box = path[dC - b + 1] ^ 1;
+          else if (b <= nCs + nSs) box = anc[dstar + 1 + (b - nCs)] ^ 1;
+          else box = S;
+          ++b;
+        }
+        if (++boxes > box_limit) {
+          atomicOr(status, kStatusIterationLimit);
+          active = false;
+        } else {
+          const float4 a = __ldg(&T.nA[box]);
+          const float4 bb = __ldg(&T.nB[box]);
+          const bool want_grad = ADJ && pass == 1 && src_j < 0;
+          float t0 = 0.0f, t1 = 1.0f;
+          bool miss = false;
+          int k0 = -1, k1 = -1;
+          if (want_grad) {
+            slab_g(0, a.x, bb.x, px, dx, ix, t0, t1, k0, k1, miss);
+            slab_g(1, a.y, bb.y, py, dy, iy, t0, t1, k0, k1, miss);
+            slab_g(2, a.z, bb.z, pz, dz, iz, t0, t1, k0, k1, miss);
+          } else {
+            slab(a.x, bb.x, px, dx, ix, t0, t1, miss);
+            slab(a.y, bb.y, py, dy, iy, t0, t1, miss);
+            slab(a.z, bb.z, pz, dz, iz, t0, t1, miss);
+          }
+          const float l = (!miss && t1 > t0) ? __fmul_rn(__fsub_rn(t1, t0), len) : 0.0f;
+          ++cnt.clip;
+          if (l > 0.0f) {
+            bool pushed = false;
+            if (P.tau_ref <= 0.0f || __fmul_rn(bb.w, l) > P.tau_ref) {
+              const int child = __ldg(&T.nT[box].x);
+              if (child >= 0) {
+                if (rsp + 2 > stack_limit) {
+                  atomicOr(status, kStatusStackOverflow);
+                  active = false;
+                } else {
+                  ++cnt.ref;
+                  rst[rsp] = child + 1;
+                  rst[rsp + 1] = child;
+                  rsp += 2;
+                }
+                pushed = true;
+              }
+            }
+            if (!pushed) {
+              if (ADJ && pass == 2) {
+                akey = box;
+                aval = -gk * fcur * l;
+              } else {
+                tau.add(a.w * l);
+                if (want_grad) {
+                  const float w = (t1 - t0) / len;
+                  const float g0 = (k1 == 0 ? -t1 * ix : 0.0f) + (k0 == 0 ? t0 * ix : 0.0f);
+                  const float g1 = (k1 == 1 ? -t1 * iy : 0.0f) + (k0 == 1 ? t0 * iy : 0.0f);
+                  const float g2 = (k1 == 2 ? -t1 * iz : 0.0f) + (k0 == 2 ? t0 * iz : 0.0f);
+                  gq0 = fmaf(a.w, g0 * len + w * dx, gq0);
+                  gq1 = fmaf(a.w, g1 * len + w * dy, gq1);
+                  gq2 = fmaf(a.w, g2 * len + w * dz, gq2);
+                }
+                ++cnt.segs;
+              }
+            }
+          }
+        }
+      }
+    }
+    if (ADJ) warp_atomic_add(J.G, akey, aval);
+  }
+  if (ADJ) {
+    // the pseudo-source's terms; every tracing lane names the same C (or source)
+    const float gf = traced ? gk * fcur : 0.0f;
+    if (src_j >= 0) {
+      warp_atomic_add(J.e, traced ? src_j : -1, gf / L);
+    } else {
+      const float c = gf / L, inv_s2 = 2.0f / s2;
+      const int key = traced ? C : -1;
+      warp_atomic_add(J.a, key, c);
+      warp_atomic_add(J.b + 0, traced ? 3 * C : -1, c * (-dx * inv_s2 - gq0));
+      warp_atomic_add(J.b + 1, traced ? 3 * C : -1, c * (-dy * inv_s2 - gq1));
+      warp_atomic_add(J.b + 2, traced ? 3 * C : -1, c * (-dz * inv_s2 - gq2));
+    }
+  }
+}
+
+// The hot path for the 32 sinks of one warp (lane holds sorted position i if
+// `has`); every lane of the warp must call it. Accumulates the lane's flux in F.
+template <bool ADJ>
+__device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P, const bool has,
+                                          const int i, const float gk, WarpStack& ws,
+                                          int* status, const AdjointArgs& J,
+                                          SinkCounters& cnt, CSum& F) {
+  const unsigned FULL = 0xffffffffu;
+  const unsigned lane = threadIdx.x & 31u;
+  const int stack_limit = P.stack_depth < kDepth ? P.stack_depth : kDepth;
+  const int box_limit = 2 * T.n_nodes_cap + 4;
+  int anc[kDepth];  // ancestors of S by depth
+  int rst[kDepth];  // this lane's cells waiting to be clipped (refinement)
+  float px = 0.0f, py = 0.0f, pz = 0.0f;
+  int S = 0, dS = 0;
+  if (has) {
+    const float4 p = T.pos[i];
+    px = p.x;
+    py = p.y;
+    pz = p.z;
+    S = T.leaf_of[i];
+    dS = __ldg(&T.ndepth[S]);
+    int u = S;
+    for (int d = dS; d >= 0; --d) {
+      anc[d] = u;
+      u = __ldg(&T.nT[u].y);
+    }
+  }
+  unsigned long long on_path = 0;
+  const unsigned live = __ballot_sync(FULL, has);
+  if (lane == 0) {
+    ws.node[0] = kRoot;
+    ws.depth[0] = 0;
+    ws.mask[0] = live;
+  }
+  int sp = live ? 1 : 0;
+  __syncwarp();
+  while (sp > 0) {
+    --sp;
+    const int X = ws.node[sp], dX = ws.depth[sp];
+    const unsigned M = ws.mask[sp];
+    __syncwarp();
+    if (lane == 0) ws.path[dX] = X;
+    const unsigned long long bit = 1ull << dX;
+    if (has) on_path = (dX <= dS && anc[dX] == X) ? (on_path | bit) : (on_path & ~bit);
+    __syncwarp();
+    const float4 s = __ldg(&T.nS[X]);
+    if (!(s.w > 0.0f)) continue;
+    bool acc = false, opn = false;
+    if ((M >> lane) & 1u) {
+      ++cnt.visit;
+      const float4 a = __ldg(&T.nA[X]);
+      const float4 bb = __ldg(&T.nB[X]);
+      const float ex = fmaxf(fmaxf(__fsub_rn(a.x, px), __fsub_rn(px, bb.x)), 0.0f);
+      const float ey = fmaxf(fmaxf(__fsub_rn(a.y, py), __fsub_rn(py, bb.y)), 0.0f);
+      const float ez = fmaxf(fmaxf(__fsub_rn(a.z, pz), __fsub_rn(pz, bb.z)), 0.0f);
+      const float r2 =
+          __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
+      acc = __ldg(&T.nl2[X]) < __fmul_rn(P.theta2, r2);
+      opn = !acc;
+    }
+    const unsigned accM = __ballot_sync(FULL, acc);
+    const unsigned opnM = __ballot_sync(FULL, opn);
+    if (accM)
+      warp_ray<ADJ>(T, P, acc, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX, s.x, s.y,
+                    s.z, s.w, -1, gk, stack_limit, box_limit, status, J, cnt, F);
+    if (opnM) {
+      const int4 t = __ldg(&T.nT[X]);
+      if (t.x < 0) {
+        for (int jj = t.z; jj < t.z + t.w; ++jj) {
+          const float4 y = __ldg(&T.src[jj]);
+          if (!(y.w > 0.0f)) continue;
+          warp_ray<ADJ>(T, P, opn, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX, y.x,
+                        y.y, y.z, y.w, jj, gk, stack_limit, box_limit, status, J, cnt, F);
+        }
+      } else {
+        if (sp + 2 > stack_limit) {
+          if (lane == 0) atomicOr(status, kStatusStackOverflow);
+          break;
+        }
+        if (lane == 0) {
+          ws.node[sp] = t.x + 1;
+          ws.depth[sp] = dX + 1;
+          ws.mask[sp] = opnM;
+          ws.node[sp + 1] = t.x;
+          ws.depth[sp + 1] = dX + 1;
+          ws.mask[sp + 1] = opnM;
+        }
+        sp += 2;
+        __syncwarp();
+      }
+    }
+  }
+}
+
+template <bool ADJ>
+__global__ void __launch_bounds__(128) walk_warp_kernel(TreeView T, const long long* sink_idx,
+                                                        int n_sink, WalkParams P, SinkOut out,
+                                                        unsigned long long* stats, int* status,
+                                                        AdjointArgs J) {
+  __shared__ WarpStack stacks[4];
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  WarpStack& ws = stacks[threadIdx.x >> 5];
+  SinkCounters cnt;
+  int i = 0, slot = 0;
+  float g = 0.0f;
+  bool has = false;
+  if (k < n_sink) {
+    PlainMap<ADJ> map{&T, sink_idx, J.grad_flux, status};
+    has = map(k, i, slot, g);
+    if (!has && !ADJ && sink_idx) {
+      if (out.flux) out.flux[k] = 0.0f;
+      if (out.counters) reinterpret_cast<int4*>(out.counters)[k] = make_int4(0, 0, 0, 0);
+    }
+  }
+  CSum F;
+  if (__any_sync(0xffffffffu, has)) warp_walk<ADJ>(T, P, has, i, g, ws, status, J, cnt, F);
+  if (!ADJ && has) {
+    if (out.flux) out.flux[slot] = F.get();
+    if (out.counters)
+      reinterpret_cast<int4*>(out.counters)[slot] = make_int4(cnt.rays, cnt.segs, cnt.visit, cnt.ref);
+  }
+  if (stats) add_stats(cnt, stats);
+}
+
+// Batched form of the warp-shared walk: each work item is cut into groups of 32
+// consecutive sinks, one warp walk per group.
+template <int BS>
+__global__ void __launch_bounds__(BS) walk_warp_batched_kernel(
+    const TreeView* __restrict__ views, float* const* __restrict__ flux_out,
+    const int2* __restrict__ items, int n_items, int item, unsigned* counter, WalkParams P,
+    unsigned long long* stats, int* status) {
+  __shared__ WarpStack stacks[BS / 32];
+  WarpStack& ws = stacks[threadIdx.x >> 5];
+  const unsigned lane = threadIdx.x & 31u;
+  SinkCounters tot;
+  while (true) {
+    unsigned it = 0;
+    if (lane == 0) it = atomicAdd(counter, 1u);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= (unsigned)n_items) break;
+    const int2 w = items[it];
+    const TreeView T = views[w.x];
+    WalkParams Pt = P;  // the coincident-source cut (1e-12 side)^2 of this tree, in fp32
+    const float smin = __fmul_rn(1e-12f, T.side);
+    Pt.smin2 = __fmul_rn(smin, smin);
+    const int end = min(w.y + item, T.n_gas);
+    for (int g0 = w.y; g0 < end; g0 += 32) {
+      const int i = g0 + (int)lane;
+      const bool has = i < end;
+      SinkCounters cnt;
+      CSum F;
+      warp_walk<false>(T, Pt, has, i, 0.0f, ws, status, AdjointArgs{}, cnt, F);
+      if (has) flux_out[w.x][T.perm[i]] = F.get();
+      tot.rays += cnt.rays;
+      tot.segs += cnt.segs;
+      tot.visit += cnt.visit;
+      tot.ref += cnt.ref;
+      tot.clip += cnt.clip;
+    }
+  }
+  if (stats) add_stats(tot, stats);
+}
+
 cudaError_t launch_walk_batched(const TreeView* views, float* const* flux_out, const int2* items,
                                 int n_items, int item, unsigned* counter, const WalkParams& wp,
                                 unsigned long long* stats, int* status, int block_size,
@@ -527,7 +879,24 @@ cudaError_t launch_walk_batched(const TreeView* views, float* const* flux_out, c
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   int per_sm = 1;
-  if (block_size <= 64) {
+  if (wp.variant == 2) {
+    const int bs = block_size <= 64 ? 64 : (block_size <= 128 ? 128 : 256);
+    if (bs == 64) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_warp_batched_kernel<64>, 64, 0);
+      walk_warp_batched_kernel<64><<<n_sm * per_sm, 64, 0, s>>>(views, flux_out, items, n_items,
+                                                                item, counter, wp, stats, status);
+    } else if (bs == 128) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_warp_batched_kernel<128>, 128,
+                                                    0);
+      walk_warp_batched_kernel<128><<<n_sm * per_sm, 128, 0, s>>>(
+          views, flux_out, items, n_items, item, counter, wp, stats, status);
+    } else {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_warp_batched_kernel<256>, 256,
+                                                    0);
+      walk_warp_batched_kernel<256><<<n_sm * per_sm, 256, 0, s>>>(
+          views, flux_out, items, n_items, item, counter, wp, stats, status);
+    }
+  } else if (block_size <= 64) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_batched_kernel<64>, 64, 0);
     walk_batched_kernel<64><<<n_sm * per_sm, 64, 0, s>>>(views, flux_out, items, n_items, item,
                                                          counter, wp, stats, status);
@@ -554,6 +923,12 @@ cudaError_t launch_walk(const TreeView& T, const long long* sink_idx, int n_sink
                         cudaStream_t s) {
   if (n_sink <= 0) return cudaSuccess;
   (void)block_size;
+  if (wp.variant == 2) {
+    walk_warp_kernel<false><<<(n_sink + 127) / 128, 128, 0, s>>>(
+        T, sink_idx, n_sink, wp, SinkOut{flux_out, counters}, stats, status, AdjointArgs{});
+    note_launch();
+    return cudaGetLastError();
+  }
   const int chunk = chunk_of(wp);
   const long long warps = ((long long)n_sink + chunk - 1) / chunk;
   const int blocks = (int)((warps * 32 + 127) / 128);
@@ -568,6 +943,12 @@ cudaError_t launch_walk_adjoint(const TreeView& T, const long long* sink_idx, in
                                 const WalkParams& wp, const AdjointArgs& J, int* status,
                                 cudaStream_t s) {
   if (n_sink <= 0) return cudaSuccess;
+  if (wp.variant == 2) {
+    walk_warp_kernel<true><<<(n_sink + 127) / 128, 128, 0, s>>>(
+        T, sink_idx, n_sink, wp, SinkOut{nullptr, nullptr}, nullptr, status, J);
+    note_launch();
+    return cudaGetLastError();
+  }
   const int chunk = chunk_of(wp);
   const long long warps = ((long long)n_sink + chunk - 1) / chunk;
   const int blocks = (int)((warps * 32 + 127) / 128);

@@ -51,7 +51,8 @@ class Domain(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("theta_open", ctypes.c_float), ("tau_ref", ctypes.c_float),
                 ("bucket", ctypes.c_int), ("sinks_per_warp", ctypes.c_int),
-                ("block_size", ctypes.c_int), ("stack_depth", ctypes.c_int)]
+                ("block_size", ctypes.c_int), ("stack_depth", ctypes.c_int),
+                ("walk_variant", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -135,9 +136,9 @@ def _stream_ptr(stream=None):
 
 
 def make_params(theta=0.75, tau_ref=0.1, bucket=8, sinks_per_warp=0, block_size=0,
-                stack_depth=0):
+                stack_depth=0, walk_variant=0):
     return Params(float(theta), float(tau_ref), int(bucket), int(sinks_per_warp),
-                  int(block_size), int(stack_depth))
+                  int(block_size), int(stack_depth), int(walk_variant))
 
 
 class Tree:

@@ -26,9 +26,10 @@ def _close(gpu, ref, rel=1e-3, floor=1e-5):
     return ok, err / np.maximum(np.abs(ref), 1e-300)
 
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("theta,tau_ref,weighted", [(0.75, 0.1, False), (0.6, 0.0, False),
                                                    (0.75, 0.1, True)])
-def test_backward_matches_oracle_adjoint(theta, tau_ref, weighted):
+def test_backward_matches_oracle_adjoint(theta, tau_ref, weighted, variant):
     import torch
     from paper_1902_08083_gb300 import trevr
     P = _lognormal(workloads.uniform_box(n_gas=6000, n_src=80, seed=50))
@@ -41,7 +42,7 @@ def test_backward_matches_oracle_adjoint(theta, tau_ref, weighted):
     gl_o, ga_o = T.adjoint(theta, tau_ref, g)
     G = gpu_tree(P)
     gl, ga = trevr.compute_flux_backward(G, torch.from_numpy(g.astype(np.float32)).cuda(), theta,
-                                         tau_ref)
+                                         tau_ref, walk_variant=variant)
     ok, rel = _close(gl.cpu().numpy(), gl_o)
     assert ok.all(), f"luminosity grads: {np.count_nonzero(~ok)} off, worst {rel.max():.3e}"
     assert np.median(rel) <= 1e-4

@@ -20,15 +20,17 @@ def trees(boxes):
     return [gpu_tree(P) for P in boxes]
 
 
-def test_batched_equals_sequential_bitwise(boxes, trees):
+@pytest.mark.parametrize("variant", [1, 2])
+def test_batched_equals_sequential_bitwise(boxes, trees, variant):
     import torch
     from paper_1902_08083_gb300 import trevr
     th, tr = boxes[0]["theta"], boxes[0]["tau_ref"]
-    seq = [trevr.compute_flux(t, th, tr) for t in trees]
-    seq_stats = [trevr.compute_flux(t, th, tr, stats=True)[1] for t in trees]
+    seq = [trevr.compute_flux(t, th, tr, walk_variant=variant) for t in trees]
+    seq_stats = [trevr.compute_flux(t, th, tr, stats=True, walk_variant=variant)[1]
+                 for t in trees]
     B = trevr.Batch(trees)
     for item, bs in ((64, 128), (32, 64), (256, 256), (96, 128)):
-        st = B.run(th, tr, stats=True, sinks_per_warp=item, block_size=bs)
+        st = B.run(th, tr, stats=True, sinks_per_warp=item, block_size=bs, walk_variant=variant)
         for b in range(len(trees)):
             assert torch.equal(B.flux[b], seq[b]), (item, bs, b)
         for k in ("interactions", "segments", "src_nodes_visited", "refine_expansions"):
@@ -81,7 +83,8 @@ def test_autotuner_picks_a_valid_shape(boxes, trees, tmp_path):
                         cache_path=str(tmp_path / "tune.json"), repeats=1)
     assert res["sinks_per_warp"] in autotune.ITEM_SIZES
     assert res["block_size"] in autotune.BLOCK_SIZES
-    assert not res["cached"] and len(res["table"]) == 12
+    assert res["walk_variant"] in autotune.VARIANTS
+    assert not res["cached"] and len(res["table"]) == 24
     again = autotune.tune(B, boxes[0]["theta"], boxes[0]["tau_ref"],
                           cache_path=str(tmp_path / "tune.json"))
     assert again["cached"] and again["sinks_per_warp"] == res["sinks_per_warp"]

@@ -27,10 +27,14 @@ def _lognormal(P, sigma=2.0, seed=1, corr=0.05):
     return P
 
 
+VARIANTS = [1, 2]  # per-lane walk, warp-shared walk
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("theta,tau_ref", [(0.75, 0.1), (0.0, 0.1), (0.75, 0.0), (0.4, 1e6)])
-def test_uniform_box_4096(theta, tau_ref):
+def test_uniform_box_4096(theta, tau_ref, variant):
     P = workloads.uniform_box(n_gas=4096, n_src=64, seed=0)
-    G, f, c, st = _run(P, theta, tau_ref)
+    G, f, c, st = _run(P, theta, tau_ref, walk_variant=variant)
     T = oracle_tree(P)
     ref, rc, margin = T.flux(theta, tau_ref, with_counters=True)
     assert_flux_parity(f, ref, f"uniform theta={theta} tau_ref={tau_ref}")
@@ -38,10 +42,11 @@ def test_uniform_box_4096(theta, tau_ref):
     assert st["interactions"] == rc[:, 0].sum() and st["segments"] == rc[:, 1].sum()
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("theta,tau_ref", [(0.75, 0.1), (0.6, 0.01), (0.75, 0.0), (0.0, 0.3)])
-def test_lognormal_refinement(theta, tau_ref):
+def test_lognormal_refinement(theta, tau_ref, variant):
     P = _lognormal(workloads.uniform_box(n_gas=12000, n_src=200, seed=21), sigma=2.0)
-    G, f, c, st = _run(P, theta, tau_ref)
+    G, f, c, st = _run(P, theta, tau_ref, walk_variant=variant)
     T = oracle_tree(P)
     ref, rc, margin = T.flux(theta, tau_ref, with_counters=True)
     assert_flux_parity(f, ref, f"lognormal theta={theta} tau_ref={tau_ref}")
@@ -50,16 +55,26 @@ def test_lognormal_refinement(theta, tau_ref):
     assert len(mism) <= max(1, len(f) // 1000), f"{len(mism)} sinks with other decisions"
 
 
-def test_weighted_cells_and_sink_subset():
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_weighted_cells_and_sink_subset(variant):
     P = _lognormal(workloads.uniform_box(n_gas=7777, n_src=100, seed=22), sigma=1.0)
     P["weight"] = np.random.default_rng(3).uniform(0.1, 4.0, 7777).astype(np.float32)
     sinks = np.random.default_rng(4).choice(7777, 1001, replace=False)
     sinks[5] = sinks[6]  # a repeated sink is allowed
-    G, f, c, _ = _run(P, 0.75, 0.1, sinks=sinks)
+    G, f, c, _ = _run(P, 0.75, 0.1, sinks=sinks, walk_variant=variant)
     T = oracle_tree(P)
     ref, rc, _ = T.flux(0.75, 0.1, sinks=sinks, with_counters=True)
     assert_flux_parity(f, ref, "weighted subset")
     np.testing.assert_array_equal(c, rc.astype(np.int32))
+
+
+_CLUMPY = {}
+
+
+def _clumpy():
+    if "P" not in _CLUMPY:
+        _CLUMPY["P"] = workloads.clumpy()
+    return _CLUMPY["P"]
 
 
 @pytest.mark.parametrize("tau_ref", [0.01, 0.1, 0.5])
@@ -79,11 +94,12 @@ def test_stromgren_closed_form(tau_ref):
     np.testing.assert_array_equal(c[sinks], oc.astype(np.int32))
 
 
-def test_clumpy_full_size_sampled():
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_clumpy_full_size_sampled(variant):
     # 2^22 gas, 2^14 clustered sources, lognormal absorption with a dense occluder;
     # the GPU computes every sink in the benchmark's launch shape, the oracle a sample
-    P = workloads.clumpy()
-    G, f, c, st = _run(P, P["theta"], P["tau_ref"])
+    P = _clumpy()
+    G, f, c, st = _run(P, P["theta"], P["tau_ref"], walk_variant=variant)
     assert np.all(np.isfinite(f)) and np.all(f >= 0)
     sinks = workloads.sink_sample(P["gas_xyz"].shape[1], 1024)
     T = oracle_tree(P)
@@ -122,9 +138,10 @@ def test_error_status_without_fault():
     from paper_1902_08083_gb300 import trevr
     P = workloads.uniform_box(n_gas=4096, n_src=64, seed=0)
     G = gpu_tree(P)
-    with pytest.raises(trevr.TrevrError) as ei:
-        trevr.compute_flux(G, 0.75, 0.1, stats=True, stack_depth=2)
-    assert ei.value.code == 3  # stack overflow reported, no trap
+    for variant in VARIANTS:
+        with pytest.raises(trevr.TrevrError) as ei:
+            trevr.compute_flux(G, 0.75, 0.1, stats=True, stack_depth=2, walk_variant=variant)
+        assert ei.value.code == 3  # stack overflow reported, no trap
     with pytest.raises(trevr.TrevrError) as ei:
         trevr.compute_flux(G, -1.0, 0.1)
     assert ei.value.code == 1
