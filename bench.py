@@ -131,6 +131,21 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
+def _walk_traffic_per_sink():
+    """DRAM bytes per sink of the walk kernel from the last ncu capture, scaled by the
+    sinks of a launch; None if the kernel source changed since that capture."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "walk_warp_kernel_dram.json")
+    try:
+        d = json.load(open(p))
+        src = open(os.path.join(ROOT, d["source"]), "rb").read()
+    except (OSError, ValueError, KeyError):
+        return None
+    if hashlib.sha256(src).hexdigest() != d["source_sha256"]:
+        return None
+    return float(d["dram_bytes_per_sink"])
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -390,11 +405,13 @@ def run_ours(args):
     # 20 B per sink (position, leaf, flux) + 32 B per source cell tested + 32 B per
     # cell clipped by a ray, divided by the walk's event-timed duration
     alg_bytes = 20 * n + 32 * st["src_nodes_visited"] + 32 * st["cells_clipped"]
+    traffic = _walk_traffic_per_sink()
+    traffic = None if traffic is None else traffic * n
     t_walk = sum(walk_ms) / len(walk_ms) * 1e-3
     peak, peak_kind = _peaks()
     achieved = alg_bytes / t_walk / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "walk_warp_kernel<false> (warp-shared sink walk + rays + flux)",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "walk_warp_kernel<false> (warp-shared sink walk + rays + flux)",
                 "peak_kind": f"{peak_kind} (copy bandwidth, burst)",
                 "bytes_per_launch": alg_bytes}
 
