@@ -66,7 +66,10 @@ typedef struct {
     int stack_depth;    /* traversal stack entries per sink, 0 = default (64) */
     int walk_variant;   /* 1 = every lane walks its own sink; 2 = the 32 lanes of a warp
                            walk one shared stack and trace together the rays to a cell
-                           they accept together; 0 = default (2) */
+                           they accept together; 3 = as 2, but each lane keeps its next
+                           ray pending and the pending rays of all lanes (to different
+                           cells) are traced together; 0 = default (3). All give the
+                           same decisions and counters. */
 } trevr_params;
 
 /* Totals over the sinks of one call, and timings (ms, CUDA events). */

@@ -17,7 +17,7 @@ import torch
 
 ITEM_SIZES = (32, 64, 128, 256)
 BLOCK_SIZES = (64, 128, 256)
-VARIANTS = (1, 2)  # per-lane walk, warp-shared walk
+VARIANTS = (1, 2, 3)  # per-lane walk, warp-shared walk, warp-shared with merged rays
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "trevr_gb300", "autotune.json")
 
 

@@ -50,7 +50,7 @@ static bool params_ok(const trevr_params* prm) {
   if (prm->stack_depth < 0 || prm->stack_depth > kMaxStack) return false;
   if (prm->block_size < 0 || prm->block_size > 1024 || (prm->block_size % 32) != 0) return false;
   if (prm->sinks_per_warp < 0) return false;
-  if (prm->walk_variant < 0 || prm->walk_variant > 2) return false;
+  if (prm->walk_variant < 0 || prm->walk_variant > 3) return false;
   return true;
 }
 
@@ -78,6 +78,7 @@ TreeView trevr_tree::view() const {
   v.nS = nS;
   v.nT = nT;
   v.nl2 = nl2;
+  v.nR = nR;
   v.ndepth = ndepth;
   v.nfirst = nfirst;
   v.ncount = ncount;
@@ -444,7 +445,7 @@ void trevr_tree_free(trevr_tree* t) {
   void* ptrs[] = {t->key, t->perm,   t->rank,   t->leaf_of, t->pos,    t->w,      t->nA,
                   t->nB,  t->nS,     t->nT,     t->nl2,     t->ndepth, t->nfirst, t->ncount,
                   t->nglo, t->nghi,  t->src,    t->src_order, t->levels, t->d_n_nodes,
-                  t->status, t->d_stats, t->src_leaf, t->nW};
+                  t->status, t->d_stats, t->src_leaf, t->nW, t->nR};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   cudaSetDevice(cur);

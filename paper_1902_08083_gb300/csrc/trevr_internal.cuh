@@ -19,7 +19,7 @@ constexpr int kMaxLevels = 66;            // depth <= 63 (one key bit per cut), 
 constexpr int kDefaultStack = 64;         // >= max depth + 1: a walk can never overflow it
 constexpr int kMaxStack = 128;
 constexpr int kDefaultChunk = 32;         // sinks per warp of the walk (one per lane)
-constexpr int kDefaultVariant = 2;        // walk variant used when the caller passes 0
+constexpr int kDefaultVariant = 3;        // walk variant used when the caller passes 0
 
 // device status bits (OR-ed by kernels, mapped to TREVR_ERR_* on the host)
 constexpr int kStatusOutOfDomain = 1;
@@ -45,6 +45,7 @@ struct TreeView {
   const float4* nS;  // (cen.x, cen.y, cen.z, L)
   const int4* nT;    // (child or -1, parent, src_first, src_count)
   const float* nl2;  // l^2 (furthest vertex from the centre of luminosity)
+  const int4* nR;    // (lower child or -1, split plane as float bits, split axis, 0)
   const int* ndepth;
   const int* nfirst;
   const int* ncount;
@@ -91,6 +92,7 @@ struct trevr_tree {
   float4* nS;
   int4* nT;
   float* nl2;
+  int4* nR;
   int* ndepth;
   int* nfirst;
   int* ncount;

@@ -42,6 +42,10 @@ constexpr int kAnc = 0;     // offsets of the three parts of the per-lane list
 constexpr int kPath = kDepth;
 constexpr int kRef = 2 * kDepth;
 constexpr float kFourPi = 12.566370614359172f;
+// refinement stack of the warp walk: refined base segments (at most 2 x 63 + 1) are
+// queued first, then each popped pair adds at most one entry per level below
+constexpr int kRayStack = 4 * kDepth;
+constexpr int kSegBuf = 64;  // segments of one ray kept for the adjoint's second pass
 
 // Neumaier-compensated fp32 sum.
 struct CSum {
@@ -595,12 +599,27 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
   const bool traced = active;
   CSum tau;
   int b = 0, rsp = 0, boxes = 0, pass = 1;
+  // adjoint: the first pass records its segment cells and lengths (up to kSegBuf),
+  // so the second pass replays them instead of tracing the ray again
+  int segb[ADJ ? kSegBuf : 1];
+  float segl[ADJ ? kSegBuf : 1];
+  int nseg = 0, kk = 0;
+  bool seg_over = false;
   float gq0 = 0.0f, gq1 = 0.0f, gq2 = 0.0f, fcur = 0.0f;
   while (__any_sync(FULL, active)) {
     int akey = -1;
     float aval = 0.0f;
-    if (active) {
-      const bool from_stack = rsp > 0;
+    if (ADJ && active && pass == 3) {
+      if (kk < nseg) {
+        akey = segb[kk];
+        aval = -gk * fcur * segl[kk];
+        ++kk;
+      } else {
+        ++cnt.rays;
+        active = false;
+      }
+    } else if (active) {
+      const bool from_stack = b >= nb && rsp > 0;  // the base segments come first
       if (!from_stack && b >= nb) {
         const float f = L * expf(-tau.get()) / (kFourPi * s2);
         if (!ADJ) {
@@ -609,10 +628,15 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
           active = false;
         } else if (pass == 1) {
           fcur = f;  // second pass over the same cells, now that f is known
-          pass = 2;
-          b = 0;
-          rsp = 0;
-          boxes = 0;
+          if (!seg_over) {
+            pass = 3;  // replay the recorded segments
+            kk = 0;
+          } else {
+            pass = 2;  // too many segments to record: trace the ray again
+            b = 0;
+            rsp = 0;
+            boxes = 0;
+          }
         } else {
           ++cnt.rays;
           active = false;
@@ -620,7 +644,13 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
       } else {
         int box;
         if (from_stack) {
-          box = rst[--rsp];
+          const int e = rst[--rsp];
+          if (e < 0) {  // a refined cell's pair of children: clip the lower, queue the upper
+            box = ~e;
+            rst[rsp++] = box + 1;
+          } else {
+            box = e;
+          }
         } else {
           if (nb == 1) box = S;
           else if (b == 0) box = C;
@@ -655,14 +685,12 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
             if (P.tau_ref <= 0.0f || __fmul_rn(bb.w, l) > P.tau_ref) {
               const int child = __ldg(&T.nT[box].x);
               if (child >= 0) {
-                if (rsp + 2 > stack_limit) {
+                if (rsp + 1 > kRayStack) {
                   atomicOr(status, kStatusStackOverflow);
                   active = false;
                 } else {
                   ++cnt.ref;
-                  rst[rsp] = child + 1;
-                  rst[rsp + 1] = child;
-                  rsp += 2;
+                  rst[rsp++] = ~child;  // both children, clipped after the base segments
                 }
                 pushed = true;
               }
@@ -673,6 +701,15 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
                 aval = -gk * fcur * l;
               } else {
                 tau.add(a.w * l);
+                if (ADJ) {
+                  if (nseg < kSegBuf) {
+                    segb[nseg] = box;
+                    segl[nseg] = l;
+                    ++nseg;
+                  } else {
+                    seg_over = true;
+                  }
+                }
                 if (want_grad) {
                   const float w = (t1 - t0) / len;
                   const float g0 = (k1 == 0 ? -t1 * ix : 0.0f) + (k0 == 0 ? t0 * ix : 0.0f);
@@ -692,24 +729,28 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
     if (ADJ) warp_atomic_add(J.G, akey, aval);
   }
   if (ADJ) {
-    // the pseudo-source's terms; every tracing lane names the same C (or source)
+    // the pseudo-source's terms. The lanes of one call may mix single sources and
+    // merged cells (merged pending rays), so every lane takes part in every
+    // warp-wide sum, naming no key (-1) for a term that is not its own.
+    const bool single = traced && src_j >= 0, merged = traced && src_j < 0;
     const float gf = traced ? gk * fcur : 0.0f;
-    if (src_j >= 0) {
-      warp_atomic_add(J.e, traced ? src_j : -1, gf / L);
-    } else {
-      const float c = gf / L, inv_s2 = 2.0f / s2;
-      const int key = traced ? C : -1;
-      warp_atomic_add(J.a, key, c);
-      warp_atomic_add(J.b + 0, traced ? 3 * C : -1, c * (-dx * inv_s2 - gq0));
-      warp_atomic_add(J.b + 1, traced ? 3 * C : -1, c * (-dy * inv_s2 - gq1));
-      warp_atomic_add(J.b + 2, traced ? 3 * C : -1, c * (-dz * inv_s2 - gq2));
-    }
+    const float c = traced ? gf / L : 0.0f, inv_s2 = 2.0f / s2;
+    warp_atomic_add(J.e, single ? src_j : -1, c);
+    warp_atomic_add(J.a, merged ? C : -1, c);
+    warp_atomic_add(J.b + 0, merged ? 3 * C : -1, c * (-dx * inv_s2 - gq0));
+    warp_atomic_add(J.b + 1, merged ? 3 * C : -1, c * (-dy * inv_s2 - gq1));
+    warp_atomic_add(J.b + 2, merged ? 3 * C : -1, c * (-dz * inv_s2 - gq2));
   }
 }
 
 // The hot path for the 32 sinks of one warp (lane holds sorted position i if
 // `has`); every lane of the warp must call it. Accumulates the lane's flux in F.
-template <bool ADJ>
+// MERGE = true: a lane that accepts a cell (or reaches a single source) does not
+// trace the ray at once; it keeps it pending, and the pending rays of all lanes are
+// traced together (each lane to its own cell) when a lane needs its slot again or
+// when the walk is about to overwrite the part of the path a pending ray uses. More
+// lanes then share each traced batch; every lane still gets the same rays.
+template <bool ADJ, bool MERGE>
 __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P, const bool has,
                                           const int i, const float gk, WarpStack& ws,
                                           int* status, const AdjointArgs& J,
@@ -718,8 +759,8 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
   const unsigned lane = threadIdx.x & 31u;
   const int stack_limit = P.stack_depth < kDepth ? P.stack_depth : kDepth;
   const int box_limit = 2 * T.n_nodes_cap + 4;
-  int anc[kDepth];  // ancestors of S by depth
-  int rst[kDepth];  // this lane's cells waiting to be clipped (refinement)
+  int anc[kDepth];     // ancestors of S by depth
+  int rst[kRayStack];  // this lane's cells waiting to be clipped (refinement)
   float px = 0.0f, py = 0.0f, pz = 0.0f;
   int S = 0, dS = 0;
   if (has) {
@@ -743,12 +784,23 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
     ws.mask[0] = live;
   }
   int sp = live ? 1 : 0;
+  // this lane's pending ray (MERGE)
+  bool pnd = false;
+  int pC = 0, pdC = 0, psrc = -1;
+  float pqx = 0.0f, pqy = 0.0f, pqz = 0.0f, pL = 0.0f;
+  auto flush = [&]() {
+    warp_ray<ADJ>(T, P, pnd, px, py, pz, S, dS, anc, rst, on_path, ws.path, pC, pdC, pqx, pqy,
+                  pqz, pL, psrc, gk, stack_limit, box_limit, status, J, cnt, F);
+    pnd = false;
+  };
   __syncwarp();
   while (sp > 0) {
     --sp;
     const int X = ws.node[sp], dX = ws.depth[sp];
     const unsigned M = ws.mask[sp];
     __syncwarp();
+    // a pending ray reads the path up to its cell's depth: trace it before that changes
+    if (MERGE && __any_sync(FULL, pnd && pdC >= dX)) flush();
     if (lane == 0) ws.path[dX] = X;
     const unsigned long long bit = 1ull << dX;
     if (has) on_path = (dX <= dS && anc[dX] == X) ? (on_path | bit) : (on_path & ~bit);
@@ -770,17 +822,44 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
     }
     const unsigned accM = __ballot_sync(FULL, acc);
     const unsigned opnM = __ballot_sync(FULL, opn);
-    if (accM)
+    if (MERGE) {
+      if (__any_sync(FULL, acc && pnd)) flush();
+      if (acc) {
+        pnd = true;
+        pC = X;
+        pdC = dX;
+        pqx = s.x;
+        pqy = s.y;
+        pqz = s.z;
+        pL = s.w;
+        psrc = -1;
+      }
+    } else if (accM) {
       warp_ray<ADJ>(T, P, acc, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX, s.x, s.y,
                     s.z, s.w, -1, gk, stack_limit, box_limit, status, J, cnt, F);
+    }
     if (opnM) {
       const int4 t = __ldg(&T.nT[X]);
       if (t.x < 0) {
         for (int jj = t.z; jj < t.z + t.w; ++jj) {
           const float4 y = __ldg(&T.src[jj]);
           if (!(y.w > 0.0f)) continue;
-          warp_ray<ADJ>(T, P, opn, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX, y.x,
-                        y.y, y.z, y.w, jj, gk, stack_limit, box_limit, status, J, cnt, F);
+          if (MERGE) {
+            if (__any_sync(FULL, opn && pnd)) flush();
+            if (opn) {
+              pnd = true;
+              pC = X;
+              pdC = dX;
+              pqx = y.x;
+              pqy = y.y;
+              pqz = y.z;
+              pL = y.w;
+              psrc = jj;
+            }
+          } else {
+            warp_ray<ADJ>(T, P, opn, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX, y.x,
+                          y.y, y.z, y.w, jj, gk, stack_limit, box_limit, status, J, cnt, F);
+          }
         }
       } else {
         if (sp + 2 > stack_limit) {
@@ -800,9 +879,10 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
       }
     }
   }
+  if (MERGE && __any_sync(FULL, pnd)) flush();
 }
 
-template <bool ADJ>
+template <bool ADJ, bool MERGE>
 __global__ void __launch_bounds__(128) walk_warp_kernel(TreeView T, const long long* sink_idx,
                                                         int n_sink, WalkParams P, SinkOut out,
                                                         unsigned long long* stats, int* status,
@@ -823,7 +903,7 @@ __global__ void __launch_bounds__(128) walk_warp_kernel(TreeView T, const long l
     }
   }
   CSum F;
-  if (__any_sync(0xffffffffu, has)) warp_walk<ADJ>(T, P, has, i, g, ws, status, J, cnt, F);
+  if (__any_sync(0xffffffffu, has)) warp_walk<ADJ, MERGE>(T, P, has, i, g, ws, status, J, cnt, F);
   if (!ADJ && has) {
     if (out.flux) out.flux[slot] = F.get();
     if (out.counters)
@@ -834,7 +914,7 @@ __global__ void __launch_bounds__(128) walk_warp_kernel(TreeView T, const long l
 
 // Batched form of the warp-shared walk: each work item is cut into groups of 32
 // consecutive sinks, one warp walk per group.
-template <int BS>
+template <int BS, bool MERGE>
 __global__ void __launch_bounds__(BS) walk_warp_batched_kernel(
     const TreeView* __restrict__ views, float* const* __restrict__ flux_out,
     const int2* __restrict__ items, int n_items, int item, unsigned* counter, WalkParams P,
@@ -859,7 +939,7 @@ __global__ void __launch_bounds__(BS) walk_warp_batched_kernel(
       const bool has = i < end;
       SinkCounters cnt;
       CSum F;
-      warp_walk<false>(T, Pt, has, i, 0.0f, ws, status, AdjointArgs{}, cnt, F);
+      warp_walk<false, MERGE>(T, Pt, has, i, 0.0f, ws, status, AdjointArgs{}, cnt, F);
       if (has) flux_out[w.x][T.perm[i]] = F.get();
       tot.rays += cnt.rays;
       tot.segs += cnt.segs;
@@ -879,23 +959,27 @@ cudaError_t launch_walk_batched(const TreeView* views, float* const* flux_out, c
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   int per_sm = 1;
-  if (wp.variant == 2) {
+  if (wp.variant >= 2) {
     const int bs = block_size <= 64 ? 64 : (block_size <= 128 ? 128 : 256);
+    const bool merge = wp.variant == 3;
+#define TREVR_WB(BSV, MV)                                                                     \
+  do {                                                                                         \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_warp_batched_kernel<BSV, MV>, \
+                                                  BSV, 0);                                     \
+    walk_warp_batched_kernel<BSV, MV><<<n_sm * per_sm, BSV, 0, s>>>(                          \
+        views, flux_out, items, n_items, item, counter, wp, stats, status);                    \
+  } while (0)
     if (bs == 64) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_warp_batched_kernel<64>, 64, 0);
-      walk_warp_batched_kernel<64><<<n_sm * per_sm, 64, 0, s>>>(views, flux_out, items, n_items,
-                                                                item, counter, wp, stats, status);
+      if (merge) TREVR_WB(64, true);
+      else TREVR_WB(64, false);
     } else if (bs == 128) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_warp_batched_kernel<128>, 128,
-                                                    0);
-      walk_warp_batched_kernel<128><<<n_sm * per_sm, 128, 0, s>>>(
-          views, flux_out, items, n_items, item, counter, wp, stats, status);
+      if (merge) TREVR_WB(128, true);
+      else TREVR_WB(128, false);
     } else {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_warp_batched_kernel<256>, 256,
-                                                    0);
-      walk_warp_batched_kernel<256><<<n_sm * per_sm, 256, 0, s>>>(
-          views, flux_out, items, n_items, item, counter, wp, stats, status);
+      if (merge) TREVR_WB(256, true);
+      else TREVR_WB(256, false);
     }
+#undef TREVR_WB
   } else if (block_size <= 64) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_batched_kernel<64>, 64, 0);
     walk_batched_kernel<64><<<n_sm * per_sm, 64, 0, s>>>(views, flux_out, items, n_items, item,
@@ -923,9 +1007,13 @@ cudaError_t launch_walk(const TreeView& T, const long long* sink_idx, int n_sink
                         cudaStream_t s) {
   if (n_sink <= 0) return cudaSuccess;
   (void)block_size;
-  if (wp.variant == 2) {
-    walk_warp_kernel<false><<<(n_sink + 127) / 128, 128, 0, s>>>(
-        T, sink_idx, n_sink, wp, SinkOut{flux_out, counters}, stats, status, AdjointArgs{});
+  if (wp.variant >= 2) {
+    if (wp.variant == 3)
+      walk_warp_kernel<false, true><<<(n_sink + 127) / 128, 128, 0, s>>>(
+          T, sink_idx, n_sink, wp, SinkOut{flux_out, counters}, stats, status, AdjointArgs{});
+    else
+      walk_warp_kernel<false, false><<<(n_sink + 127) / 128, 128, 0, s>>>(
+          T, sink_idx, n_sink, wp, SinkOut{flux_out, counters}, stats, status, AdjointArgs{});
     note_launch();
     return cudaGetLastError();
   }
@@ -943,9 +1031,13 @@ cudaError_t launch_walk_adjoint(const TreeView& T, const long long* sink_idx, in
                                 const WalkParams& wp, const AdjointArgs& J, int* status,
                                 cudaStream_t s) {
   if (n_sink <= 0) return cudaSuccess;
-  if (wp.variant == 2) {
-    walk_warp_kernel<true><<<(n_sink + 127) / 128, 128, 0, s>>>(
-        T, sink_idx, n_sink, wp, SinkOut{nullptr, nullptr}, nullptr, status, J);
+  if (wp.variant >= 2) {
+    if (wp.variant == 3)
+      walk_warp_kernel<true, true><<<(n_sink + 127) / 128, 128, 0, s>>>(
+          T, sink_idx, n_sink, wp, SinkOut{nullptr, nullptr}, nullptr, status, J);
+    else
+      walk_warp_kernel<true, false><<<(n_sink + 127) / 128, 128, 0, s>>>(
+          T, sink_idx, n_sink, wp, SinkOut{nullptr, nullptr}, nullptr, status, J);
     note_launch();
     return cudaGetLastError();
   }

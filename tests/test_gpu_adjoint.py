@@ -26,7 +26,7 @@ def _close(gpu, ref, rel=1e-3, floor=1e-5):
     return ok, err / np.maximum(np.abs(ref), 1e-300)
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("theta,tau_ref,weighted", [(0.75, 0.1, False), (0.6, 0.0, False),
                                                    (0.75, 0.1, True)])
 def test_backward_matches_oracle_adjoint(theta, tau_ref, weighted, variant):

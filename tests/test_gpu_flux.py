@@ -27,7 +27,7 @@ def _lognormal(P, sigma=2.0, seed=1, corr=0.05):
     return P
 
 
-VARIANTS = [1, 2]  # per-lane walk, warp-shared walk
+VARIANTS = [1, 2, 3]  # per-lane walk, warp-shared walk, warp-shared with merged rays
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
