@@ -134,6 +134,24 @@ int trevr_compute_flux(const trevr_tree* t, const long long* sink_idx, long long
                        trevr_stats* stats, void* stream);
 
 /*
+ * The flux and its next two direction moments at the sinks (Sec. 2.1: the
+ * vector flux of Eq. simpflux, F = sum of L exp(-tau)/(4 pi s^2) n over the
+ * pseudo-sources with n the unit vector from the pseudo-source to the sink, and
+ * the radiation-pressure moment sum of the same terms times n n^T), from the
+ * same walk, rays and decisions as trevr_compute_flux.
+ *
+ *   t, sink_idx, n_sink, prm  as in trevr_compute_flux (walk_variant ignored).
+ *   flux_out  n_sink floats (Eq. simpint), as trevr_compute_flux.
+ *   fvec_out  3*n_sink floats, SoA: x[0..n), y[0..n), z[0..n).
+ *   press_out NULL or 6*n_sink floats, SoA in the order xx, yy, zz, xy, xz, yz
+ *             (its trace equals flux_out).
+ * Synchronises the stream and reports device errors.
+ */
+int trevr_compute_flux_moments(const trevr_tree* t, const long long* sink_idx, long long n_sink,
+                               const trevr_params* prm, float* flux_out, float* fvec_out,
+                               float* press_out, void* stream);
+
+/*
  * Gradients of a scalar loss through the flux, with the decisions of the
  * forward pass held fixed (the merge/open choices of Eq. openangle, the
  * refinement choices of Eq. refcrit and the cells each ray touches): the

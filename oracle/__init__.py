@@ -73,6 +73,8 @@ def _load():
         lib.orc_export_sources.restype = None
         lib.orc_flux.argtypes = [P, P, i64, f32, f32, P, P, P, ctypes.c_int]
         lib.orc_flux.restype = ctypes.c_int
+        lib.orc_flux_moments.argtypes = [P, P, i64, f32, f32, P, P, P, ctypes.c_int]
+        lib.orc_flux_moments.restype = ctypes.c_int
         lib.orc_sink_interactions.argtypes = [P, i64, f32, f32, i64] + [P] * 8
         lib.orc_sink_interactions.restype = i64
         lib.orc_ray_tau.argtypes = [P, i64, i64, P, f32, P, P]
@@ -223,6 +225,22 @@ class OracleTree:
         if rc != ORC_OK:
             raise OracleError(rc)
         return (flux, cnt, mar) if with_counters else flux
+
+    def flux_moments(self, theta, tau_ref, sinks=None, nthreads=0):
+        """(flux[n], flux vector[n,3] = sum f n, pressure[n,6] = sum f n n^T (xx,yy,zz,xy,xz,yz)),
+        n the unit vector from each pseudo-source to the sink (Eq. simpflux)."""
+        if sinks is None:
+            sinks = np.arange(self.n_gas, dtype=np.int64)
+        sinks = np.ascontiguousarray(sinks, dtype=np.int64)
+        n = sinks.shape[0]
+        flux = np.zeros(n)
+        fvec = np.zeros((n, 3))
+        press = np.zeros((n, 6))
+        rc = self._lib.orc_flux_moments(self._h, _ptr(sinks), n, float(theta), float(tau_ref),
+                                        _ptr(flux), _ptr(fvec), _ptr(press), int(nthreads))
+        if rc != ORC_OK:
+            raise OracleError(rc)
+        return flux, fvec, press
 
     def interactions(self, sink, theta, tau_ref, cap=1 << 16):
         """Interaction list of one sink: node C, q, L, tau, summed length, flux, nseg, src."""

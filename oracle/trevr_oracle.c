@@ -623,7 +623,10 @@ static void note_margin(counters_t *c, double m)
     if (m < c->margin) c->margin = m;
 }
 
-/* fp32 length of the ray inside the node box (slab method); 0 if it misses. */
+/* fp32 length of the ray inside the node box (slab method); 0 if it misses.
+   Along an axis the ray does not move on (d_k = 0) the box is half-open,
+   [lo, hi): a ray lying in a face between two cells belongs to the upper one
+   only, so the cells still tile the ray exactly. */
 static float clip32(const ray_t *R, const float blo[3], const float bhi[3])
 {
     float t0 = 0.0f, t1 = 1.0f;
@@ -633,7 +636,7 @@ static float clip32(const ray_t *R, const float blo[3], const float bhi[3])
             float tb = (bhi[k] - R->p[k]) * R->inv[k];
             t0 = fmaxf(t0, fminf(ta, tb));
             t1 = fminf(t1, fmaxf(ta, tb));
-        } else if (R->p[k] < blo[k] || R->p[k] > bhi[k]) {
+        } else if (R->p[k] < blo[k] || R->p[k] >= bhi[k]) {
             return 0.0f;
         }
     }
@@ -652,7 +655,7 @@ static double clip64(const orc_tree *T, const ray_t *R, int64_t X)
             double tb = (hi - R->P[k]) / R->D[k];
             t0 = fmax(t0, fmin(ta, tb));
             t1 = fmin(t1, fmax(ta, tb));
-        } else if (R->P[k] < lo || R->P[k] > hi) {
+        } else if (R->P[k] < lo || R->P[k] >= hi) {
             return 0.0;
         }
     }
@@ -744,10 +747,30 @@ typedef struct {
     int64_t n, cap;
 } inter_log_t;
 
+/* Moments of the intensity beyond Eq. simpint (Sec. 2.1): the flux vector
+   sum f n (Eq. simpflux, n the unit vector from the source to the sink) and the
+   second moment sum f n n^T (radiation pressure tensor; xx, yy, zz, xy, xz, yz). */
+typedef struct {
+    nsum_t v[9];
+} moments_t;
+
+static moments_t *g_no_moments = NULL;
+
 /* One pseudo-source (L at q, inside node C) seen from sorted particle i. */
+static double contribute_m(const orc_tree *T, int64_t i, int64_t S, int64_t C, const float q32[3],
+                           const double q64[3], double L, float tau_ref, float smin2,
+                           counters_t *c, inter_log_t *log, int64_t src, moments_t *mom);
+
 static double contribute(const orc_tree *T, int64_t i, int64_t S, int64_t C, const float q32[3],
                          const double q64[3], double L, float tau_ref, float smin2,
                          counters_t *c, inter_log_t *log, int64_t src)
+{
+    return contribute_m(T, i, S, C, q32, q64, L, tau_ref, smin2, c, log, src, g_no_moments);
+}
+
+static double contribute_m(const orc_tree *T, int64_t i, int64_t S, int64_t C, const float q32[3],
+                           const double q64[3], double L, float tau_ref, float smin2,
+                           counters_t *c, inter_log_t *log, int64_t src, moments_t *mom)
 {
     ray_t R;
     R.p[0] = T->px[i];
@@ -771,6 +794,16 @@ static double contribute(const orc_tree *T, int64_t i, int64_t S, int64_t C, con
     /* Eq. simpint: I = L exp(-tau) / (4 pi s^2) */
     double f = L * exp(-tau) / (4.0 * M_PI * S2);
     c->interactions++;
+    if (mom) {
+        const double n[3] = {-R.D[0] / R.LEN, -R.D[1] / R.LEN, -R.D[2] / R.LEN};
+        for (int k = 0; k < 3; ++k) nsum_add(&mom->v[k], f * n[k]);
+        nsum_add(&mom->v[3], f * n[0] * n[0]);
+        nsum_add(&mom->v[4], f * n[1] * n[1]);
+        nsum_add(&mom->v[5], f * n[2] * n[2]);
+        nsum_add(&mom->v[6], f * n[0] * n[1]);
+        nsum_add(&mom->v[7], f * n[0] * n[2]);
+        nsum_add(&mom->v[8], f * n[1] * n[2]);
+    }
     if (log && log->n < log->cap) {
         inter_t *e = &log->buf[log->n];
         e->node = C;
@@ -793,8 +826,17 @@ static double contribute(const orc_tree *T, int64_t i, int64_t S, int64_t C, con
  * otherwise it is opened; a leaf that is opened contributes its sources one
  * by one.  fp32 decision: l^2 < theta^2 r^2.
  */
+static double sink_flux_m(const orc_tree *T, int64_t i, float theta, float tau_ref,
+                          counters_t *c, inter_log_t *log, moments_t *mom);
+
 static double sink_flux(const orc_tree *T, int64_t i, float theta, float tau_ref,
                         counters_t *c, inter_log_t *log)
+{
+    return sink_flux_m(T, i, theta, tau_ref, c, log, NULL);
+}
+
+static double sink_flux_m(const orc_tree *T, int64_t i, float theta, float tau_ref,
+                          counters_t *c, inter_log_t *log, moments_t *mom)
 {
     const float theta2 = theta * theta;
     const float smin = 1e-12f * T->side32;
@@ -826,15 +868,15 @@ static double sink_flux(const orc_tree *T, int64_t i, float theta, float tau_ref
             if (den > 0.0) note_margin(c, fabs(l - tr) / den);
         }
         if (accept) {
-            nsum_add(&F, contribute(T, i, S, X, T->cen32[X], T->cen[X], T->L[X], tau_ref, smin2, c,
-                                    log, -1));
+            nsum_add(&F, contribute_m(T, i, S, X, T->cen32[X], T->cen[X], T->L[X], tau_ref, smin2,
+                                      c, log, -1, mom));
         } else if (T->split_bit[X] < 0) {
             for (int64_t s = T->src_first[X]; s < T->src_first[X] + T->src_count[X]; ++s) {
                 if (!(T->slum[s] > 0.0f)) continue;
                 const float q32[3] = {T->sx[s], T->sy[s], T->sz[s]};
                 const double q64[3] = {(double)T->sx[s], (double)T->sy[s], (double)T->sz[s]};
-                nsum_add(&F, contribute(T, i, S, X, q32, q64, (double)T->slum[s], tau_ref, smin2,
-                                        c, log, s));
+                nsum_add(&F, contribute_m(T, i, S, X, q32, q64, (double)T->slum[s], tau_ref, smin2,
+                                          c, log, s, mom));
             }
         } else {
             stack[sp++] = T->upper[X];
@@ -873,6 +915,36 @@ int orc_flux(const orc_tree *T, const int64_t *sinks, int64_t n_sink, float thet
             counters[4 * k + 3] = c.refinements;
         }
         if (margin) margin[k] = c.margin;
+    }
+    return ORC_OK;
+}
+
+/*
+ * Flux and its first two direction moments at the sinks: flux[k] (Eq. simpint),
+ * fvec[3k..3k+2] = sum f n (Eq. simpflux) and press[6k..6k+5] = sum f n n^T
+ * (xx, yy, zz, xy, xz, yz), n the unit vector from the pseudo-source to the sink.
+ */
+int orc_flux_moments(const orc_tree *T, const int64_t *sinks, int64_t n_sink, float theta,
+                     float tau_ref, double *flux, double *fvec, double *press, int nthreads)
+{
+    if (!(theta >= 0.0f) || !isfinite(theta) || isnan(tau_ref)) return ORC_ERR_INVALID_ARGUMENT;
+    for (int64_t k = 0; k < n_sink; ++k)
+        if (sinks[k] < 0 || sinks[k] >= T->n_gas) return ORC_ERR_INVALID_ARGUMENT;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t k = 0; k < n_sink; ++k) {
+        counters_t c;
+        memset(&c, 0, sizeof(c));
+        c.margin = INFINITY;
+        moments_t m;
+        memset(&m, 0, sizeof(m));
+        flux[k] = sink_flux_m(T, T->rank[sinks[k]], theta, tau_ref, &c, NULL, &m);
+        for (int q = 0; q < 3; ++q)
+            if (fvec) fvec[3 * k + q] = nsum_get(&m.v[q]);
+        for (int q = 0; q < 6; ++q)
+            if (press) press[6 * k + q] = nsum_get(&m.v[3 + q]);
     }
     return ORC_OK;
 }
@@ -982,7 +1054,7 @@ static double clip64_grad(const orc_tree *T, const ray_t *R, int64_t X, double g
             double tn = fmin(ta, tb), tx = fmax(ta, tb);
             if (tn > t0) { t0 = tn; k0 = k; }
             if (tx < t1) { t1 = tx; k1 = k; }
-        } else if (R->P[k] < lo || R->P[k] > hi) {
+        } else if (R->P[k] < lo || R->P[k] >= hi) {
             grad[0] = grad[1] = grad[2] = 0.0;
             return 0.0;
         }
@@ -1335,7 +1407,7 @@ static double seg_len64(const orc_tree *T, const double P[3], const double Q[3],
             double ta = (lo - P[k]) / D[k], tb = (hi - P[k]) / D[k];
             t0 = fmax(t0, fmin(ta, tb));
             t1 = fmin(t1, fmax(ta, tb));
-        } else if (P[k] < lo || P[k] > hi) {
+        } else if (P[k] < lo || P[k] >= hi) {
             return 0.0;
         }
     }

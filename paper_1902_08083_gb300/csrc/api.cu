@@ -78,7 +78,6 @@ TreeView trevr_tree::view() const {
   v.nS = nS;
   v.nT = nT;
   v.nl2 = nl2;
-  v.nR = nR;
   v.ndepth = ndepth;
   v.nfirst = nfirst;
   v.ncount = ncount;
@@ -153,6 +152,31 @@ int trevr_compute_flux(const trevr_tree* t, const long long* sink_idx, long long
   stats->refine_expansions = (long long)h[3];
   stats->cells_clipped = (long long)h[4];
   stats->walk_ms = ms;
+  if (status) {
+    cudaMemsetAsync(t->status, 0, sizeof(int), s);
+    cudaStreamSynchronize(s);
+    return status_to_error(status);
+  }
+  return TREVR_OK;
+}
+
+int trevr_compute_flux_moments(const trevr_tree* t, const long long* sink_idx, long long n_sink,
+                               const trevr_params* prm, float* flux_out, float* fvec_out,
+                               float* press_out, void* stream) {
+  if (!t || !params_ok(prm)) return TREVR_ERR_INVALID_ARGUMENT;
+  if (n_sink < 0 || n_sink > (1ll << 30)) return TREVR_ERR_INVALID_ARGUMENT;
+  if (n_sink == 0) return TREVR_OK;
+  if (!flux_out || !fvec_out) return TREVR_ERR_INVALID_ARGUMENT;
+  if (!sink_idx && n_sink != t->n_gas) return TREVR_ERR_INVALID_ARGUMENT;
+  cudaStream_t s = (cudaStream_t)stream;
+  WalkParams wp = walk_params(t, prm);
+  cudaError_t err = launch_walk_moments(t->view(), sink_idx, (int)n_sink, wp, flux_out, fvec_out,
+                                        press_out, t->status, s);
+  if (err != cudaSuccess) return cuda_to_error(err);
+  int status = 0;
+  cudaMemcpyAsync(&status, t->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) return cuda_to_error(err);
   if (status) {
     cudaMemsetAsync(t->status, 0, sizeof(int), s);
     cudaStreamSynchronize(s);
@@ -445,7 +469,7 @@ void trevr_tree_free(trevr_tree* t) {
   void* ptrs[] = {t->key, t->perm,   t->rank,   t->leaf_of, t->pos,    t->w,      t->nA,
                   t->nB,  t->nS,     t->nT,     t->nl2,     t->ndepth, t->nfirst, t->ncount,
                   t->nglo, t->nghi,  t->src,    t->src_order, t->levels, t->d_n_nodes,
-                  t->status, t->d_stats, t->src_leaf, t->nW, t->nR};
+                  t->status, t->d_stats, t->src_leaf, t->nW};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   cudaSetDevice(cur);

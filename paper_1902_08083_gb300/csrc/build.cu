@@ -451,7 +451,6 @@ struct MomentArrays {
   float4* nB;
   float4* nS;
   float* nl2;
-  int4* nR;
   float lo[3], h;
 };
 
@@ -541,15 +540,6 @@ __global__ void moments_level_kernel(MomentArrays A, int L) {
     A.nB[X] = make_float4(bhi[0], bhi[1], bhi[2], dal);
     A.nS[X] = make_float4(c[0], c[1], c[2], Lf);
     A.nl2[X] = l2;
-    if (t.x >= 0) {
-      // the cut between the children: plane on axis a at the upper child's lower face
-      const int a = A.nglo[X].w;
-      const int4 gu = A.nglo[t.x + 1];
-      const int ga = a == 0 ? gu.x : (a == 1 ? gu.y : gu.z);
-      A.nR[X] = make_int4(t.x, __float_as_int(world(A.lo[a], A.h, ga)), a, 0);
-    } else {
-      A.nR[X] = make_int4(-1, 0, -1, 0);
-    }
   }
 }
 
@@ -738,7 +728,6 @@ int build_tree_impl(const float* gas_xyz, const float* alpha, const float* weigh
   t->nB = keep.get<float4>(ncell);
   t->nS = keep.get<float4>(ncell);
   t->nl2 = keep.get<float>(ncell);
-  t->nR = keep.get<int4>(ncell);
   t->nW = keep.get<double>(ncell);
   Moments* mom = tmp.get<Moments>(ncell);
   if (!keep.ok || !tmp.ok) {
@@ -750,7 +739,6 @@ int build_tree_impl(const float* gas_xyz, const float* alpha, const float* weigh
   cudaMemsetAsync(t->nB, 0, sizeof(float4), s);
   cudaMemsetAsync(t->nS, 0, sizeof(float4), s);
   cudaMemsetAsync(t->nl2, 0, sizeof(float), s);
-  cudaMemsetAsync(t->nR, 0xff, sizeof(int4), s);
   cudaMemsetAsync(t->nW, 0, sizeof(double), s);
   MomentArrays MA;
   MA.nT = t->nT;
@@ -768,7 +756,6 @@ int build_tree_impl(const float* gas_xyz, const float* alpha, const float* weigh
   MA.nB = t->nB;
   MA.nS = t->nS;
   MA.nl2 = t->nl2;
-  MA.nR = t->nR;
   for (int d = 0; d < 3; ++d) MA.lo[d] = t->lo[d];
   MA.h = t->h;
   for (int L = max_depth; L >= 0; --L) {

@@ -45,7 +45,6 @@ struct TreeView {
   const float4* nS;  // (cen.x, cen.y, cen.z, L)
   const int4* nT;    // (child or -1, parent, src_first, src_count)
   const float* nl2;  // l^2 (furthest vertex from the centre of luminosity)
-  const int4* nR;    // (lower child or -1, split plane as float bits, split axis, 0)
   const int* ndepth;
   const int* nfirst;
   const int* ncount;
@@ -92,7 +91,6 @@ struct trevr_tree {
   float4* nS;
   int4* nT;
   float* nl2;
-  int4* nR;
   int* ndepth;
   int* nfirst;
   int* ncount;
@@ -158,6 +156,9 @@ cudaError_t launch_walk_batched(const TreeView* views, float* const* flux_out, c
                                 int n_items, int item, unsigned* counter, const WalkParams& wp,
                                 unsigned long long* stats, int* status, int block_size,
                                 int n_sm, cudaStream_t s);
+cudaError_t launch_walk_moments(const TreeView& T, const long long* sink_idx, int n_sink,
+                                const WalkParams& wp, float* flux_out, float* fvec, float* press,
+                                int* status, cudaStream_t s);
 cudaError_t launch_walk(const TreeView& T, const long long* sink_idx, int n_sink,
                         const WalkParams& wp, float* flux_out, int* counters,
                         unsigned long long* stats, int* status, int block_size,

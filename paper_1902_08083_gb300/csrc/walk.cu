@@ -59,7 +59,9 @@ struct CSum {
   __device__ __forceinline__ float get() const { return __fadd_rn(s, c); }
 };
 
-// one slab of the clip: (lo - p) * (1/d), (hi - p) * (1/d), rounded after each step
+// one slab of the clip: (lo - p) * (1/d), (hi - p) * (1/d), rounded after each step;
+// along an axis the ray does not move on, the box is half-open [lo, hi), so a ray
+// lying in the face between two cells belongs to the upper one only
 __device__ __forceinline__ void slab(float lo, float hi, float p, float d, float inv, float& t0,
                                      float& t1, bool& miss) {
   if (d != 0.0f) {
@@ -68,7 +70,7 @@ __device__ __forceinline__ void slab(float lo, float hi, float p, float d, float
     t0 = fmaxf(t0, fminf(ta, tb));
     t1 = fminf(t1, fmaxf(ta, tb));
   } else {
-    miss = miss || p < lo || p > hi;
+    miss = miss || p < lo || p >= hi;
   }
 }
 
@@ -88,7 +90,7 @@ __device__ __forceinline__ void slab_g(int k, float lo, float hi, float p, float
       k1 = k;
     }
   } else {
-    miss = miss || p < lo || p > hi;
+    miss = miss || p < lo || p >= hi;
   }
 }
 
@@ -376,6 +378,15 @@ struct Lane {
 struct SinkOut {
   float* flux;    // flux per sink (caller order), or nullptr
   int* counters;  // 4 int per sink, or nullptr
+  float* fvec;    // flux vector, 3 x n_sink (SoA), or nullptr
+  float* press;   // second moment, 6 x n_sink (SoA: xx yy zz xy xz yz), or nullptr
+  int n_out;      // n_sink (stride of the SoA blocks)
+};
+
+// Direction moments of the intensity at one sink: sum f n and sum f n n^T, n the
+// unit vector from the pseudo-source to the sink (Eq. simpflux; Sec. 2.1).
+struct Moments {
+  CSum v[9];  // x y z | xx yy zz xy xz yz
 };
 
 // Runs the sinks [first, end) of a chunk with one warp: the lanes start on the
@@ -516,7 +527,7 @@ __global__ void __launch_bounds__(BS) walk_batched_kernel(const TreeView* __rest
     WalkParams Pt = P;  // the coincident-source cut (1e-12 side)^2 of this tree, in fp32
     const float smin = __fmul_rn(1e-12f, T.side);
     Pt.smin2 = __fmul_rn(smin, smin);
-    SinkOut out{flux_out[w.x], nullptr};
+    SinkOut out{flux_out[w.x], nullptr, nullptr, nullptr, 0};
     TreeMap map{&T};
     run_chunk<false>(T, Pt, w.y, min(w.y + item, T.n_gas), map, out, status, AdjointArgs{}, tot);
   }
@@ -559,7 +570,7 @@ __device__ __forceinline__ void warp_atomic_add(double* base, int key, float v) 
 
 // Rays from the sinks of the lanes in `on` to (q, L) inside cell C; every lane
 // of the warp must call it (the loop runs while any lane has cells left).
-template <bool ADJ>
+template <bool ADJ, bool MOM>
 __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P, const bool on,
                                          const float px, const float py, const float pz,
                                          const int S, const int dS, const int* anc, int* rst,
@@ -568,7 +579,7 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
                                          const float qy, const float qz, const float L,
                                          const int src_j, const float gk, const int stack_limit,
                                          const int box_limit, int* status, const AdjointArgs& J,
-                                         SinkCounters& cnt, CSum& F) {
+                                         SinkCounters& cnt, CSum& F, Moments* mom) {
   const unsigned FULL = 0xffffffffu;
   float dx = 0.0f, dy = 0.0f, dz = 0.0f, s2 = 1.0f, len = 1.0f, ix = 0.0f, iy = 0.0f, iz = 0.0f;
   int nCs = 0, nSs = 0, nb = 0, dstar = 0;
@@ -624,6 +635,19 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
         const float f = L * expf(-tau.get()) / (kFourPi * s2);
         if (!ADJ) {
           F.add(f);
+          if (MOM) {
+            const float il = 1.0f / len;
+            const float n0 = -dx * il, n1 = -dy * il, n2 = -dz * il;
+            mom->v[0].add(f * n0);
+            mom->v[1].add(f * n1);
+            mom->v[2].add(f * n2);
+            mom->v[3].add(f * n0 * n0);
+            mom->v[4].add(f * n1 * n1);
+            mom->v[5].add(f * n2 * n2);
+            mom->v[6].add(f * n0 * n1);
+            mom->v[7].add(f * n0 * n2);
+            mom->v[8].add(f * n1 * n2);
+          }
           ++cnt.rays;
           active = false;
         } else if (pass == 1) {
@@ -750,11 +774,11 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
 // traced together (each lane to its own cell) when a lane needs its slot again or
 // when the walk is about to overwrite the part of the path a pending ray uses. More
 // lanes then share each traced batch; every lane still gets the same rays.
-template <bool ADJ, bool MERGE>
+template <bool ADJ, bool MERGE, bool MOM = false>
 __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P, const bool has,
                                           const int i, const float gk, WarpStack& ws,
                                           int* status, const AdjointArgs& J,
-                                          SinkCounters& cnt, CSum& F) {
+                                          SinkCounters& cnt, CSum& F, Moments* mom = nullptr) {
   const unsigned FULL = 0xffffffffu;
   const unsigned lane = threadIdx.x & 31u;
   const int stack_limit = P.stack_depth < kDepth ? P.stack_depth : kDepth;
@@ -789,8 +813,8 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
   int pC = 0, pdC = 0, psrc = -1;
   float pqx = 0.0f, pqy = 0.0f, pqz = 0.0f, pL = 0.0f;
   auto flush = [&]() {
-    warp_ray<ADJ>(T, P, pnd, px, py, pz, S, dS, anc, rst, on_path, ws.path, pC, pdC, pqx, pqy,
-                  pqz, pL, psrc, gk, stack_limit, box_limit, status, J, cnt, F);
+    warp_ray<ADJ, MOM>(T, P, pnd, px, py, pz, S, dS, anc, rst, on_path, ws.path, pC, pdC, pqx,
+                       pqy, pqz, pL, psrc, gk, stack_limit, box_limit, status, J, cnt, F, mom);
     pnd = false;
   };
   __syncwarp();
@@ -835,8 +859,8 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
         psrc = -1;
       }
     } else if (accM) {
-      warp_ray<ADJ>(T, P, acc, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX, s.x, s.y,
-                    s.z, s.w, -1, gk, stack_limit, box_limit, status, J, cnt, F);
+      warp_ray<ADJ, MOM>(T, P, acc, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX, s.x,
+                         s.y, s.z, s.w, -1, gk, stack_limit, box_limit, status, J, cnt, F, mom);
     }
     if (opnM) {
       const int4 t = __ldg(&T.nT[X]);
@@ -857,8 +881,9 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
               psrc = jj;
             }
           } else {
-            warp_ray<ADJ>(T, P, opn, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX, y.x,
-                          y.y, y.z, y.w, jj, gk, stack_limit, box_limit, status, J, cnt, F);
+            warp_ray<ADJ, MOM>(T, P, opn, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX,
+                               y.x, y.y, y.z, y.w, jj, gk, stack_limit, box_limit, status, J, cnt,
+                               F, mom);
           }
         }
       } else {
@@ -882,7 +907,7 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
   if (MERGE && __any_sync(FULL, pnd)) flush();
 }
 
-template <bool ADJ, bool MERGE>
+template <bool ADJ, bool MERGE, bool MOM = false>
 __global__ void __launch_bounds__(128) walk_warp_kernel(TreeView T, const long long* sink_idx,
                                                         int n_sink, WalkParams P, SinkOut out,
                                                         unsigned long long* stats, int* status,
@@ -903,7 +928,17 @@ __global__ void __launch_bounds__(128) walk_warp_kernel(TreeView T, const long l
     }
   }
   CSum F;
-  if (__any_sync(0xffffffffu, has)) warp_walk<ADJ, MERGE>(T, P, has, i, g, ws, status, J, cnt, F);
+  Moments mom;
+  if (__any_sync(0xffffffffu, has))
+    warp_walk<ADJ, MERGE, MOM>(T, P, has, i, g, ws, status, J, cnt, F, MOM ? &mom : nullptr);
+  if (MOM && has) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      if (out.fvec) out.fvec[(size_t)q * out.n_out + slot] = mom.v[q].get();
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+      if (out.press) out.press[(size_t)q * out.n_out + slot] = mom.v[3 + q].get();
+  }
   if (!ADJ && has) {
     if (out.flux) out.flux[slot] = F.get();
     if (out.counters)
@@ -997,6 +1032,17 @@ cudaError_t launch_walk_batched(const TreeView* views, float* const* flux_out, c
   return cudaGetLastError();
 }
 
+cudaError_t launch_walk_moments(const TreeView& T, const long long* sink_idx, int n_sink,
+                                const WalkParams& wp, float* flux_out, float* fvec, float* press,
+                                int* status, cudaStream_t s) {
+  if (n_sink <= 0) return cudaSuccess;
+  walk_warp_kernel<false, true, true><<<(n_sink + 127) / 128, 128, 0, s>>>(
+      T, sink_idx, n_sink, wp, SinkOut{flux_out, nullptr, fvec, press, n_sink}, nullptr, status,
+      AdjointArgs{});
+  note_launch();
+  return cudaGetLastError();
+}
+
 static int chunk_of(const WalkParams& wp) {
   return wp.sinks_per_warp > 0 ? wp.sinks_per_warp : kDefaultChunk;
 }
@@ -1010,10 +1056,10 @@ cudaError_t launch_walk(const TreeView& T, const long long* sink_idx, int n_sink
   if (wp.variant >= 2) {
     if (wp.variant == 3)
       walk_warp_kernel<false, true><<<(n_sink + 127) / 128, 128, 0, s>>>(
-          T, sink_idx, n_sink, wp, SinkOut{flux_out, counters}, stats, status, AdjointArgs{});
+          T, sink_idx, n_sink, wp, SinkOut{flux_out, counters, nullptr, nullptr, n_sink}, stats, status, AdjointArgs{});
     else
       walk_warp_kernel<false, false><<<(n_sink + 127) / 128, 128, 0, s>>>(
-          T, sink_idx, n_sink, wp, SinkOut{flux_out, counters}, stats, status, AdjointArgs{});
+          T, sink_idx, n_sink, wp, SinkOut{flux_out, counters, nullptr, nullptr, n_sink}, stats, status, AdjointArgs{});
     note_launch();
     return cudaGetLastError();
   }
@@ -1021,7 +1067,7 @@ cudaError_t launch_walk(const TreeView& T, const long long* sink_idx, int n_sink
   const long long warps = ((long long)n_sink + chunk - 1) / chunk;
   const int blocks = (int)((warps * 32 + 127) / 128);
   walk_kernel<false><<<blocks, 128, 0, s>>>(T, sink_idx, n_sink, chunk, wp,
-                                            SinkOut{flux_out, counters}, stats, status,
+                                            SinkOut{flux_out, counters, nullptr, nullptr, n_sink}, stats, status,
                                             AdjointArgs{});
   note_launch();
   return cudaGetLastError();
@@ -1034,10 +1080,10 @@ cudaError_t launch_walk_adjoint(const TreeView& T, const long long* sink_idx, in
   if (wp.variant >= 2) {
     if (wp.variant == 3)
       walk_warp_kernel<true, true><<<(n_sink + 127) / 128, 128, 0, s>>>(
-          T, sink_idx, n_sink, wp, SinkOut{nullptr, nullptr}, nullptr, status, J);
+          T, sink_idx, n_sink, wp, SinkOut{nullptr, nullptr, nullptr, nullptr, n_sink}, nullptr, status, J);
     else
       walk_warp_kernel<true, false><<<(n_sink + 127) / 128, 128, 0, s>>>(
-          T, sink_idx, n_sink, wp, SinkOut{nullptr, nullptr}, nullptr, status, J);
+          T, sink_idx, n_sink, wp, SinkOut{nullptr, nullptr, nullptr, nullptr, n_sink}, nullptr, status, J);
     note_launch();
     return cudaGetLastError();
   }
@@ -1045,7 +1091,7 @@ cudaError_t launch_walk_adjoint(const TreeView& T, const long long* sink_idx, in
   const long long warps = ((long long)n_sink + chunk - 1) / chunk;
   const int blocks = (int)((warps * 32 + 127) / 128);
   walk_kernel<true><<<blocks, 128, 0, s>>>(T, sink_idx, n_sink, chunk, wp,
-                                           SinkOut{nullptr, nullptr}, nullptr, status, J);
+                                           SinkOut{nullptr, nullptr, nullptr, nullptr, n_sink}, nullptr, status, J);
   note_launch();
   return cudaGetLastError();
 }

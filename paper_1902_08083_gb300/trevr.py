@@ -28,7 +28,8 @@ ERRORS = {
 
 # names of every entry point declared in include/trevr.h
 EXPORTS = (
-    "trevr_build_tree", "trevr_compute_flux", "trevr_compute_flux_backward", "trevr_check",
+    "trevr_build_tree", "trevr_compute_flux", "trevr_compute_flux_backward",
+    "trevr_compute_flux_moments", "trevr_check",
     "trevr_tree_info",
     "trevr_tree_export", "trevr_tree_free", "trevr_status_string", "trevr_kernel_launches",
     "trevr_morton_sort_noalloc", "trevr_batch_create", "trevr_compute_flux_batched",
@@ -99,6 +100,8 @@ def load_library(path: str = LIB_PATH):
         lib.trevr_batch_check.restype = ctypes.c_int
         lib.trevr_batch_free.argtypes = [P]
         lib.trevr_batch_free.restype = None
+        lib.trevr_compute_flux_moments.argtypes = [P, P, ll, ctypes.POINTER(Params), P, P, P, P]
+        lib.trevr_compute_flux_moments.restype = ctypes.c_int
         lib.trevr_check.argtypes = [P, P]
         lib.trevr_check.restype = ctypes.c_int
         lib.trevr_tree_info.argtypes = [P, ctypes.POINTER(ll), ctypes.POINTER(ctypes.c_int),
@@ -271,6 +274,27 @@ def morton_sort_noalloc(gas_xyz, lo=(0.0, 0.0, 0.0), side=1.0, keys_out=None, pe
     if rc != TREVR_OK:
         raise TrevrError(rc, "trevr_morton_sort_noalloc")
     return keys_out, perm_out
+
+
+def compute_flux_moments(tree: Tree, theta=0.75, tau_ref=0.1, sink_idx=None, pressure=True,
+                         stream=None, **tuning):
+    """(flux[n], flux vector[3, n], pressure[6, n] or None) at the sinks
+    (trevr_compute_flux_moments): sum f, sum f n, sum f n n^T (xx yy zz xy xz yz)."""
+    lib = tree._lib
+    n = tree.n_gas if sink_idx is None else int(sink_idx.shape[0])
+    dev = tree.device
+    flux = torch.empty(n, dtype=torch.float32, device=dev)
+    fvec = torch.empty(3, n, dtype=torch.float32, device=dev)
+    press = torch.empty(6, n, dtype=torch.float32, device=dev) if pressure else None
+    prm = make_params(theta, tau_ref, tree.bucket, **tuning)
+    rc = lib.trevr_compute_flux_moments(tree.handle, _dev_ptr(sink_idx, torch.int64, "sink_idx"),
+                                        n, ctypes.byref(prm), _dev_ptr(flux, torch.float32, "f"),
+                                        _dev_ptr(fvec, torch.float32, "fvec"),
+                                        _dev_ptr(press, torch.float32, "press"),
+                                        _stream_ptr(stream))
+    if rc != TREVR_OK:
+        raise TrevrError(rc, "trevr_compute_flux_moments")
+    return flux, fvec, press
 
 
 def compute_flux_backward(tree: Tree, grad_flux, theta=0.75, tau_ref=0.1, sink_idx=None,

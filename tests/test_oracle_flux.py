@@ -43,7 +43,7 @@ def _clip_all(lo, hi, p, q):
             t0 = np.maximum(t0, np.minimum(ta, tb))
             t1 = np.minimum(t1, np.maximum(ta, tb))
         else:
-            out = (p[k] < lo[:, k]) | (p[k] > hi[:, k])
+            out = (p[k] < lo[:, k]) | (p[k] >= hi[:, k])  # half-open along a still axis
             t1 = np.where(out, -1.0, t1)
     return np.maximum(t1 - t0, 0.0) * np.linalg.norm(d)
 
