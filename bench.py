@@ -154,10 +154,11 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def _oracle_baseline(P, n_gas, sample_n, seed=7):
-    """Time the FP64 oracle as it stands on the host cores on a bounded sample:
-    the full tree build plus the flux at `sample_n` sinks. Returns (value, info, sinks,
-    flux)."""
+def _oracle_baseline(P, n_gas, sample_n, seconds, seed=7):
+    """Time the FP64 oracle as it stands on the host cores on a bounded sample: the
+    full tree build, the flux at `sample_n` seeded sinks (also the parity sample),
+    then the flux at as many further seeded sinks as take about `seconds` of walking,
+    the timed sample. Returns (info, parity sinks, their flux, tree)."""
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
@@ -168,11 +169,16 @@ def _oracle_baseline(P, n_gas, sample_n, seed=7):
     sinks = workloads.sink_sample(n_gas, sample_n, seed=seed)
     t0 = time.perf_counter()
     f = T.flux(P["theta"], P["tau_ref"], sinks=sinks, nthreads=cores)
+    t_pilot = time.perf_counter() - t0
+    m = int(min(n_gas, max(len(sinks), seconds * len(sinks) / max(t_pilot, 1e-6))))
+    timed = workloads.sink_sample(n_gas, m, seed=seed + 1)
+    t0 = time.perf_counter()
+    T.flux(P["theta"], P["tau_ref"], sinks=timed, nthreads=cores)
     t_walk = time.perf_counter() - t0
     # build time is charged in proportion to the sample's share of the sinks
-    per_sink = t_walk / len(sinks) + t_build / n_gas
+    per_sink = t_walk / m + t_build / n_gas
     info = {"value": 1.0 / per_sink, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{len(sinks)} of {n_gas} sinks walked (seeded) + the full {n_gas}-particle "
+            "sample": f"{m} of {n_gas} sinks walked (seeded) + the full {n_gas}-particle "
                       f"tree build charged pro rata; walk {t_walk:.2f} s, build {t_build:.2f} s",
             "walk_s": t_walk, "build_s": t_build}
     return info, sinks, f, T
@@ -191,7 +197,13 @@ def run_reference(args):
     T = oracle.OracleTree(P["gas_xyz"], P["alpha"], P["src_xyz"], P["src_lum"], lo=P["lo"],
                           side=P["side"], bucket=P["bucket"])
     t_build = time.perf_counter() - t0
-    sample_n = min(n, args.ref_sample)
+    # each step walks a seeded sample sized from a pilot so that the whole run takes
+    # about --ref-seconds of walking
+    pilot = workloads.sink_sample(n, min(n, 1024), seed=99)
+    t0 = time.perf_counter()
+    T.flux(P["theta"], P["tau_ref"], sinks=pilot, nthreads=cores)
+    per = (time.perf_counter() - t0) / len(pilot)
+    sample_n = int(min(n, max(256, args.ref_seconds / (args.warmup + args.steps) / per)))
     times = []
     for step in range(args.warmup + args.steps):
         sinks = workloads.sink_sample(n, sample_n, seed=100 + step)
@@ -296,6 +308,42 @@ def _bench_adjoint(args):
     return {"workload": f"{n} gas, {P['src_xyz'].shape[1]} sources, lognormal sigma_ln=1",
             "forward_ms": min(fwd), "backward_ms": min(bwd),
             "backward_sinks_per_s": n / (min(bwd) * 1e-3)}
+
+
+def _bench_termination(args, P, g):
+    """Early ray termination (Sec. 5) on an optically thick copy of the workload: the
+    same particles and sources with every absorption coefficient x16. Times the walk
+    with and without tau_stop = 10 and checks the bound 0 <= F - F_stop <=
+    exp(-tau_stop) F(alpha = 0) at every sink."""
+    import torch
+    from paper_1902_08083_gb300 import trevr
+    stream = torch.cuda.current_stream()
+    tau_stop = 10.0
+    thick = (g["alpha"] * 16.0).contiguous()
+    zero = torch.zeros_like(g["alpha"])
+    kw = dict(lo=P["lo"], side=P["side"], bucket=P["bucket"])
+    tree = trevr.build_tree(g["gas_xyz"], thick, g["src_xyz"], g["src_lum"], **kw)
+    tree0 = trevr.build_tree(g["gas_xyz"], zero, g["src_xyz"], g["src_lum"], **kw)
+    F = trevr.compute_flux(tree, P["theta"], P["tau_ref"])
+    Fs, st = trevr.compute_flux(tree, P["theta"], P["tau_ref"], tau_stop=tau_stop, stats=True)
+    F0 = trevr.compute_flux(tree0, P["theta"], P["tau_ref"])
+    plain = _time_ms(lambda: trevr.compute_flux(tree, P["theta"], P["tau_ref"], out=F),
+                     args.steps, stream)
+    stop = _time_ms(lambda: trevr.compute_flux(tree, P["theta"], P["tau_ref"], out=Fs,
+                                               tau_stop=tau_stop), args.steps, stream)
+    d = F.double() - Fs.double()
+    bound = float(np.exp(-tau_stop)) * F0.double()
+    # fp32 rounding of the two sums: a relative 1e-5 of F beside the bound
+    ok = bool(torch.all(d >= -1e-5 * F.double()) and torch.all(d <= bound * 1.01 + 1e-5 * F))
+    rel = d.abs() / F.double().clamp_min(1e-30)
+    tree.free()
+    tree0.free()
+    return {"workload": f"{P['gas_xyz'].shape[1]} gas, {P['src_xyz'].shape[1]} sources, "
+                        f"alpha x16", "tau_stop": tau_stop,
+            "walk_ms": min(plain), "walk_ms_terminated": min(stop),
+            "speedup": min(plain) / min(stop),
+            "rays_terminated_frac": st["rays_terminated"] / max(st["interactions"], 1),
+            "median_rel_change": float(rel.median()), "bound_holds": ok}
 
 
 def run_ours(args):
@@ -434,9 +482,10 @@ def run_ours(args):
     if world == 1 and not args.no_extras:
         line["batched"] = _bench_batched(args)
         line["adjoint"] = _bench_adjoint(args)
+        line["terminated"] = _bench_termination(args, P, g)
 
     if world == 1 and not args.no_cpu_baseline:
-        info, sinks, fo, _ = _oracle_baseline(P, n, args.cpu_sample)
+        info, sinks, fo, _ = _oracle_baseline(P, n, args.cpu_sample, args.cpu_seconds)
         fg = flux.cpu().numpy()[sinks].astype(np.float64)
         big = fo >= 1e-30
         rel = np.abs(fg[big] - fo[big]) / fo[big]
@@ -483,7 +532,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="clumpy", choices=["clumpy", "stromgren", "uniform"])
     ap.add_argument("--cpu-sample", type=int, default=2048)
-    ap.add_argument("--ref-sample", type=int, default=512)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="seconds of oracle walking timed for cpu_baseline")
+    ap.add_argument("--ref-seconds", type=float, default=90.0,
+                    help="seconds of oracle walking over all steps of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched (64 boxes) and adjoint (2^21) measurements")

@@ -70,6 +70,17 @@ typedef struct {
                            ray pending and the pending rays of all lanes (to different
                            cells) are traced together; 0 = default (3). All give the
                            same decisions and counters. */
+    float bg_radius;    /* > 0: every source is a background source on the sphere of this
+                           radius around the domain centre (Sec. 2.2.4), and a merged cell's
+                           centre of luminosity is moved radially onto that sphere before
+                           its ray is traced (the ray then ends in the leaf holding the
+                           moved point). 0 = off. Only trevr_compute_flux accepts it. */
+    float tau_stop;     /* > 0: early ray termination (Sec. 5, proposed there): a ray's
+                           optical depth sum stops once it exceeds tau_stop, and the ray
+                           then adds nothing (the flux drops by at most exp(-tau_stop)
+                           times its unabsorbed value). The fp32 running sum decides.
+                           0 = off; negative or NaN is an invalid argument. Only
+                           trevr_compute_flux accepts it. */
 } trevr_params;
 
 /* Totals over the sinks of one call, and timings (ms, CUDA events). */
@@ -81,6 +92,7 @@ typedef struct {
     long long cells_clipped;     /* ray/cell intersection tests (every cell record a ray read) */
     float build_ms;
     float walk_ms;
+    long long rays_terminated;   /* rays cut off by tau_stop (of the interactions) */
 } trevr_stats;
 
 /*

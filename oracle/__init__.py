@@ -75,7 +75,11 @@ def _load():
         lib.orc_flux.restype = ctypes.c_int
         lib.orc_flux_moments.argtypes = [P, P, i64, f32, f32, P, P, P, ctypes.c_int]
         lib.orc_flux_moments.restype = ctypes.c_int
-        lib.orc_sink_interactions.argtypes = [P, i64, f32, f32, i64] + [P] * 8
+        lib.orc_flux_background.argtypes = [P, P, i64, f32, f32, f32, P, P, ctypes.c_int]
+        lib.orc_flux_background.restype = ctypes.c_int
+        lib.orc_flux_terminated.argtypes = [P, P, i64, f32, f32, f32, f32, P, P, ctypes.c_int]
+        lib.orc_flux_terminated.restype = ctypes.c_int
+        lib.orc_sink_interactions.argtypes = [P, i64, f32, f32, f32, i64] + [P] * 8
         lib.orc_sink_interactions.restype = i64
         lib.orc_ray_tau.argtypes = [P, i64, i64, P, f32, P, P]
         lib.orc_ray_tau.restype = ctypes.c_double
@@ -226,6 +230,41 @@ class OracleTree:
             raise OracleError(rc)
         return (flux, cnt, mar) if with_counters else flux
 
+    def flux_background(self, theta, tau_ref, radius, sinks=None, nthreads=0,
+                        with_counters=False):
+        """Flux with all sources treated as background sources on the sphere of `radius`
+        around the domain centre: merged centroids are moved onto the sphere (Sec. 2.2.4)."""
+        if sinks is None:
+            sinks = np.arange(self.n_gas, dtype=np.int64)
+        sinks = np.ascontiguousarray(sinks, dtype=np.int64)
+        n = sinks.shape[0]
+        flux = np.zeros(n)
+        cnt = np.zeros((n, 4), np.int64) if with_counters else None
+        rc = self._lib.orc_flux_background(self._h, _ptr(sinks), n, float(theta), float(tau_ref),
+                                           float(radius), _ptr(flux), _ptr(cnt), int(nthreads))
+        if rc != ORC_OK:
+            raise OracleError(rc)
+        return (flux, cnt) if with_counters else flux
+
+    def flux_terminated(self, theta, tau_ref, tau_stop, sinks=None, nthreads=0,
+                        with_counters=False, bg_radius=0.0):
+        """Flux with early ray termination (Sec. 5): a ray whose optical depth passes
+        tau_stop > 0 adds nothing (bg_radius > 0: with the background sources of
+        flux_background). counters columns: interactions, segments, visited source nodes,
+        refinements (of the complete rays), terminated rays."""
+        if sinks is None:
+            sinks = np.arange(self.n_gas, dtype=np.int64)
+        sinks = np.ascontiguousarray(sinks, dtype=np.int64)
+        n = sinks.shape[0]
+        flux = np.zeros(n)
+        cnt = np.zeros((n, 5), np.int64) if with_counters else None
+        rc = self._lib.orc_flux_terminated(self._h, _ptr(sinks), n, float(theta), float(tau_ref),
+                                           float(tau_stop), float(bg_radius), _ptr(flux),
+                                           _ptr(cnt), int(nthreads))
+        if rc != ORC_OK:
+            raise OracleError(rc)
+        return (flux, cnt) if with_counters else flux
+
     def flux_moments(self, theta, tau_ref, sinks=None, nthreads=0):
         """(flux[n], flux vector[n,3] = sum f n, pressure[n,6] = sum f n n^T (xx,yy,zz,xy,xz,yz)),
         n the unit vector from each pseudo-source to the sink (Eq. simpflux)."""
@@ -242,13 +281,13 @@ class OracleTree:
             raise OracleError(rc)
         return flux, fvec, press
 
-    def interactions(self, sink, theta, tau_ref, cap=1 << 16):
+    def interactions(self, sink, theta, tau_ref, cap=1 << 16, bg_radius=0.0):
         """Interaction list of one sink: node C, q, L, tau, summed length, flux, nseg, src."""
         out = dict(node=np.zeros(cap, np.int64), q=np.zeros((cap, 3)), L=np.zeros(cap),
                    tau=np.zeros(cap), len_sum=np.zeros(cap), flux=np.zeros(cap),
                    nseg=np.zeros(cap, np.int64), src=np.zeros(cap, np.int64))
         n = self._lib.orc_sink_interactions(
-            self._h, int(sink), float(theta), float(tau_ref), cap,
+            self._h, int(sink), float(theta), float(tau_ref), float(bg_radius), cap,
             *(_ptr(out[k]) for k in ("node", "q", "L", "tau", "len_sum", "flux", "nseg", "src")))
         if n < 0 or n > cap:
             raise OracleError(ORC_ERR_NO_MEMORY)

@@ -612,7 +612,7 @@ static void nsum_add(nsum_t *s, double x)
 static double nsum_get(const nsum_t *s) { return s->sum + s->comp; }
 
 typedef struct {
-    int64_t interactions, segments, visited, refinements;
+    int64_t interactions, segments, visited, refinements, terminated;
     double margin;
     /* optional record of the frozen decisions */
     int record;
@@ -759,18 +759,25 @@ static moments_t *g_no_moments = NULL;
 /* One pseudo-source (L at q, inside node C) seen from sorted particle i. */
 static double contribute_m(const orc_tree *T, int64_t i, int64_t S, int64_t C, const float q32[3],
                            const double q64[3], double L, float tau_ref, float smin2,
-                           counters_t *c, inter_log_t *log, int64_t src, moments_t *mom);
+                           counters_t *c, inter_log_t *log, int64_t src, moments_t *mom,
+                           float tau_stop);
 
 static double contribute(const orc_tree *T, int64_t i, int64_t S, int64_t C, const float q32[3],
                          const double q64[3], double L, float tau_ref, float smin2,
                          counters_t *c, inter_log_t *log, int64_t src)
 {
-    return contribute_m(T, i, S, C, q32, q64, L, tau_ref, smin2, c, log, src, g_no_moments);
+    return contribute_m(T, i, S, C, q32, q64, L, tau_ref, smin2, c, log, src, g_no_moments,
+                        0.0f);
 }
 
+/* tau_stop > 0: early ray termination (Sec. 5, proposed there). The optical depth
+   sum of a ray is abandoned once it passes tau_stop, and the ray then adds nothing.
+   Every term of the sum is non-negative, so a partial sum passes tau_stop exactly
+   when the complete sum does: here the complete sum decides. */
 static double contribute_m(const orc_tree *T, int64_t i, int64_t S, int64_t C, const float q32[3],
                            const double q64[3], double L, float tau_ref, float smin2,
-                           counters_t *c, inter_log_t *log, int64_t src, moments_t *mom)
+                           counters_t *c, inter_log_t *log, int64_t src, moments_t *mom,
+                           float tau_stop)
 {
     ray_t R;
     R.p[0] = T->px[i];
@@ -791,9 +798,11 @@ static double contribute_m(const orc_tree *T, int64_t i, int64_t S, int64_t C, c
     memset(&rs, 0, sizeof(rs));
     ray_tau(T, &R, S, C, tau_ref, c, &rs);
     double tau = nsum_get(&rs.tau);
+    const int cut = tau_stop > 0.0f && tau > (double)tau_stop;
     /* Eq. simpint: I = L exp(-tau) / (4 pi s^2) */
-    double f = L * exp(-tau) / (4.0 * M_PI * S2);
+    double f = cut ? 0.0 : L * exp(-tau) / (4.0 * M_PI * S2);
     c->interactions++;
+    c->terminated += cut;
     if (mom) {
         const double n[3] = {-R.D[0] / R.LEN, -R.D[1] / R.LEN, -R.D[2] / R.LEN};
         for (int k = 0; k < 3; ++k) nsum_add(&mom->v[k], f * n[k]);
@@ -827,16 +836,61 @@ static double contribute_m(const orc_tree *T, int64_t i, int64_t S, int64_t C, c
  * by one.  fp32 decision: l^2 < theta^2 r^2.
  */
 static double sink_flux_m(const orc_tree *T, int64_t i, float theta, float tau_ref,
-                          counters_t *c, inter_log_t *log, moments_t *mom);
+                          counters_t *c, inter_log_t *log, moments_t *mom, float bg_radius,
+                          float tau_stop);
 
 static double sink_flux(const orc_tree *T, int64_t i, float theta, float tau_ref,
                         counters_t *c, inter_log_t *log)
 {
-    return sink_flux_m(T, i, theta, tau_ref, c, log, NULL);
+    return sink_flux_m(T, i, theta, tau_ref, c, log, NULL, 0.0f, 0.0f);
+}
+
+/* Leaf holding a point that may sit a rounding step outside the domain: its grid
+   coordinates are clamped to the grid. */
+static int64_t leaf_of_point_clamped(const orc_tree *T, const float q[3])
+{
+    const float scale = domain_scale32(T->side32);
+    uint32_t g[3];
+    for (int d = 0; d < 3; ++d) {
+        float t = (q[d] - T->lo32[d]) * scale;
+        if (!(t >= 0.0f)) t = 0.0f;
+        uint32_t v = (uint32_t)t;
+        g[d] = v > (uint32_t)(GRID_MAX - 1) ? (uint32_t)(GRID_MAX - 1) : v;
+    }
+    return leaf_of_point(T, g);
+}
+
+/*
+ * Background sources (Sec. 2.2.4): all sources lie on a sphere of radius R
+ * around the centre of the domain, and a merged cell's centre of luminosity,
+ * which lies inside the sphere, is moved radially onto it before the ray is
+ * traced; the ray then ends in the leaf that holds the moved point. fp32
+ * position (it drives the decisions): d = c - o; s = sqrt((dx^2 + dy^2) + dz^2);
+ * k = R / s; q = o + d * k, with o = lo + side * 0.5. A centroid at the centre
+ * itself is not moved.
+ */
+static void bg_project(const orc_tree *T, const float c32[3], const double c64[3], float R,
+                       float q32[3], double q64[3])
+{
+    float o[3], d[3];
+    double O[3], D[3];
+    for (int k = 0; k < 3; ++k) {
+        o[k] = T->lo32[k] + T->side32 * 0.5f;
+        d[k] = c32[k] - o[k];
+        O[k] = T->lo[k] + 0.5 * T->side;
+        D[k] = c64[k] - O[k];
+    }
+    float s = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double S = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+    for (int k = 0; k < 3; ++k) {
+        q32[k] = s > 0.0f ? o[k] + d[k] * (R / s) : c32[k];
+        q64[k] = S > 0.0 ? O[k] + D[k] * ((double)R / S) : c64[k];
+    }
 }
 
 static double sink_flux_m(const orc_tree *T, int64_t i, float theta, float tau_ref,
-                          counters_t *c, inter_log_t *log, moments_t *mom)
+                          counters_t *c, inter_log_t *log, moments_t *mom, float bg_radius,
+                          float tau_stop)
 {
     const float theta2 = theta * theta;
     const float smin = 1e-12f * T->side32;
@@ -867,16 +921,23 @@ static double sink_flux_m(const orc_tree *T, int64_t i, float theta, float tau_r
             double den = fmax(tr, l);
             if (den > 0.0) note_margin(c, fabs(l - tr) / den);
         }
-        if (accept) {
+        if (accept && bg_radius > 0.0f) {
+            float q32[3];
+            double q64[3];
+            bg_project(T, T->cen32[X], T->cen[X], bg_radius, q32, q64);
+            const int64_t Cq = leaf_of_point_clamped(T, q32);
+            nsum_add(&F, contribute_m(T, i, S, Cq, q32, q64, T->L[X], tau_ref, smin2, c, log, -1,
+                                      mom, tau_stop));
+        } else if (accept) {
             nsum_add(&F, contribute_m(T, i, S, X, T->cen32[X], T->cen[X], T->L[X], tau_ref, smin2,
-                                      c, log, -1, mom));
+                                      c, log, -1, mom, tau_stop));
         } else if (T->split_bit[X] < 0) {
             for (int64_t s = T->src_first[X]; s < T->src_first[X] + T->src_count[X]; ++s) {
                 if (!(T->slum[s] > 0.0f)) continue;
                 const float q32[3] = {T->sx[s], T->sy[s], T->sz[s]};
                 const double q64[3] = {(double)T->sx[s], (double)T->sy[s], (double)T->sz[s]};
                 nsum_add(&F, contribute_m(T, i, S, X, q32, q64, (double)T->slum[s], tau_ref, smin2,
-                                          c, log, s, mom));
+                                          c, log, s, mom, tau_stop));
             }
         } else {
             stack[sp++] = T->upper[X];
@@ -940,7 +1001,7 @@ int orc_flux_moments(const orc_tree *T, const int64_t *sinks, int64_t n_sink, fl
         c.margin = INFINITY;
         moments_t m;
         memset(&m, 0, sizeof(m));
-        flux[k] = sink_flux_m(T, T->rank[sinks[k]], theta, tau_ref, &c, NULL, &m);
+        flux[k] = sink_flux_m(T, T->rank[sinks[k]], theta, tau_ref, &c, NULL, &m, 0.0f, 0.0f);
         for (int q = 0; q < 3; ++q)
             if (fvec) fvec[3 * k + q] = nsum_get(&m.v[q]);
         for (int q = 0; q < 6; ++q)
@@ -949,11 +1010,77 @@ int orc_flux_moments(const orc_tree *T, const int64_t *sinks, int64_t n_sink, fl
     return ORC_OK;
 }
 
+/* Flux with every source treated as a background source on the sphere of radius
+   bg_radius around the domain centre (merged centroids moved onto the sphere). */
+int orc_flux_background(const orc_tree *T, const int64_t *sinks, int64_t n_sink, float theta,
+                        float tau_ref, float bg_radius, double *flux, int64_t *counters,
+                        int nthreads)
+{
+    if (!(theta >= 0.0f) || !isfinite(theta) || isnan(tau_ref) || !(bg_radius > 0.0f))
+        return ORC_ERR_INVALID_ARGUMENT;
+    for (int64_t k = 0; k < n_sink; ++k)
+        if (sinks[k] < 0 || sinks[k] >= T->n_gas) return ORC_ERR_INVALID_ARGUMENT;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t k = 0; k < n_sink; ++k) {
+        counters_t c;
+        memset(&c, 0, sizeof(c));
+        c.margin = INFINITY;
+        flux[k] = sink_flux_m(T, T->rank[sinks[k]], theta, tau_ref, &c, NULL, NULL, bg_radius,
+                              0.0f);
+        if (counters) {
+            counters[4 * k + 0] = c.interactions;
+            counters[4 * k + 1] = c.segments;
+            counters[4 * k + 2] = c.visited;
+            counters[4 * k + 3] = c.refinements;
+        }
+    }
+    return ORC_OK;
+}
+
+/* Flux with early ray termination at optical depth tau_stop > 0 (Sec. 5), and
+   with background sources on the sphere of radius bg_radius when it is > 0.
+   counters (nullable) gets 5 int64 per sink: interactions, segments, visited
+   source nodes, refinements and terminated rays (segments and refinements
+   count the complete rays). */
+int orc_flux_terminated(const orc_tree *T, const int64_t *sinks, int64_t n_sink, float theta,
+                        float tau_ref, float tau_stop, float bg_radius, double *flux,
+                        int64_t *counters, int nthreads)
+{
+    if (!(theta >= 0.0f) || !isfinite(theta) || isnan(tau_ref) || !(tau_stop > 0.0f) ||
+        !(bg_radius >= 0.0f))
+        return ORC_ERR_INVALID_ARGUMENT;
+    for (int64_t k = 0; k < n_sink; ++k)
+        if (sinks[k] < 0 || sinks[k] >= T->n_gas) return ORC_ERR_INVALID_ARGUMENT;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t k = 0; k < n_sink; ++k) {
+        counters_t c;
+        memset(&c, 0, sizeof(c));
+        c.margin = INFINITY;
+        flux[k] = sink_flux_m(T, T->rank[sinks[k]], theta, tau_ref, &c, NULL, NULL, bg_radius,
+                              tau_stop);
+        if (counters) {
+            counters[5 * k + 0] = c.interactions;
+            counters[5 * k + 1] = c.segments;
+            counters[5 * k + 2] = c.visited;
+            counters[5 * k + 3] = c.refinements;
+            counters[5 * k + 4] = c.terminated;
+        }
+    }
+    return ORC_OK;
+}
+
 /* Interaction list of one sink (caller index): returns the number of
    interactions; fills at most cap entries. */
 int64_t orc_sink_interactions(const orc_tree *T, int64_t sink, float theta, float tau_ref,
-                              int64_t cap, int64_t *node, double *q, double *L, double *tau,
-                              double *len_sum, double *flux, int64_t *nseg, int64_t *src)
+                              float bg_radius, int64_t cap, int64_t *node, double *q, double *L,
+                              double *tau, double *len_sum, double *flux, int64_t *nseg,
+                              int64_t *src)
 {
     inter_log_t log;
     log.n = 0;
@@ -963,7 +1090,7 @@ int64_t orc_sink_interactions(const orc_tree *T, int64_t sink, float theta, floa
     counters_t c;
     memset(&c, 0, sizeof(c));
     c.margin = INFINITY;
-    sink_flux(T, T->rank[sink], theta, tau_ref, &c, &log);
+    sink_flux_m(T, T->rank[sink], theta, tau_ref, &c, &log, NULL, bg_radius, 0.0f);
     for (int64_t k = 0; k < log.n && k < cap; ++k) {
         const inter_t *e = &log.buf[k];
         if (node) node[k] = e->node;

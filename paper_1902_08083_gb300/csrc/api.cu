@@ -40,6 +40,10 @@ static WalkParams walk_params(const trevr_tree* t, const trevr_params* prm) {
   wp.stack_depth = prm->stack_depth > 0 ? prm->stack_depth : kDefaultStack;
   wp.sinks_per_warp = prm->sinks_per_warp;
   wp.variant = prm->walk_variant > 0 ? prm->walk_variant : kDefaultVariant;
+  wp.bg_radius = prm->bg_radius;
+  wp.tau_stop = prm->tau_stop > 0.0f ? prm->tau_stop : INFINITY;
+  // background sources and early termination are built into the merged-ray walk only
+  if (wp.bg_radius > 0.0f || prm->tau_stop > 0.0f) wp.variant = 3;
   return wp;
 }
 
@@ -51,6 +55,8 @@ static bool params_ok(const trevr_params* prm) {
   if (prm->block_size < 0 || prm->block_size > 1024 || (prm->block_size % 32) != 0) return false;
   if (prm->sinks_per_warp < 0) return false;
   if (prm->walk_variant < 0 || prm->walk_variant > 3) return false;
+  if (!(prm->bg_radius >= 0.0f) || !std::isfinite(prm->bg_radius)) return false;
+  if (!(prm->tau_stop >= 0.0f)) return false;
   return true;
 }
 
@@ -79,6 +85,7 @@ TreeView trevr_tree::view() const {
   v.nT = nT;
   v.nl2 = nl2;
   v.ndepth = ndepth;
+  v.nglo = nglo;
   v.nfirst = nfirst;
   v.ncount = ncount;
   v.src = src;
@@ -122,7 +129,7 @@ int trevr_compute_flux(const trevr_tree* t, const long long* sink_idx, long long
   WalkParams wp = walk_params(t, prm);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (stats) {
-    cudaMemsetAsync(t->d_stats, 0, 5 * sizeof(unsigned long long), s);
+    cudaMemsetAsync(t->d_stats, 0, 6 * sizeof(unsigned long long), s);
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
@@ -136,7 +143,7 @@ int trevr_compute_flux(const trevr_tree* t, const long long* sink_idx, long long
   }
   if (!stats) return TREVR_OK;
   cudaEventRecord(e1, s);
-  unsigned long long h[5];
+  unsigned long long h[6];
   int status = 0;
   cudaMemcpyAsync(h, t->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(&status, t->status, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -151,6 +158,7 @@ int trevr_compute_flux(const trevr_tree* t, const long long* sink_idx, long long
   stats->src_nodes_visited = (long long)h[2];
   stats->refine_expansions = (long long)h[3];
   stats->cells_clipped = (long long)h[4];
+  stats->rays_terminated = (long long)h[5];
   stats->walk_ms = ms;
   if (status) {
     cudaMemsetAsync(t->status, 0, sizeof(int), s);
@@ -165,6 +173,7 @@ int trevr_compute_flux_moments(const trevr_tree* t, const long long* sink_idx, l
                                float* press_out, void* stream) {
   if (!t || !params_ok(prm)) return TREVR_ERR_INVALID_ARGUMENT;
   if (n_sink < 0 || n_sink > (1ll << 30)) return TREVR_ERR_INVALID_ARGUMENT;
+  if (prm->bg_radius > 0.0f || prm->tau_stop > 0.0f) return TREVR_ERR_INVALID_ARGUMENT;
   if (n_sink == 0) return TREVR_OK;
   if (!flux_out || !fvec_out) return TREVR_ERR_INVALID_ARGUMENT;
   if (!sink_idx && n_sink != t->n_gas) return TREVR_ERR_INVALID_ARGUMENT;
@@ -191,6 +200,7 @@ int trevr_compute_flux_backward(const trevr_tree* t, const long long* sink_idx, 
   if (!t || !params_ok(prm)) return TREVR_ERR_INVALID_ARGUMENT;
   if (n_sink < 0 || n_sink > (1ll << 30)) return TREVR_ERR_INVALID_ARGUMENT;
   if (n_sink > 0 && !grad_flux) return TREVR_ERR_INVALID_ARGUMENT;
+  if (prm->bg_radius > 0.0f || prm->tau_stop > 0.0f) return TREVR_ERR_INVALID_ARGUMENT;
   if (n_sink > 0 && !sink_idx && n_sink != t->n_gas) return TREVR_ERR_INVALID_ARGUMENT;
   if ((t->n_src > 0 && !grad_lum) || !grad_alpha) return TREVR_ERR_INVALID_ARGUMENT;
   cudaStream_t s = (cudaStream_t)stream;
@@ -287,6 +297,7 @@ static int batch_items(trevr_batch* B, int item) {
 int trevr_compute_flux_batched(trevr_batch* B, const trevr_params* prm, float* const* flux_out,
                                trevr_stats* stats, void* stream) {
   if (!B || !flux_out || !params_ok(prm)) return TREVR_ERR_INVALID_ARGUMENT;
+  if (prm->bg_radius > 0.0f || prm->tau_stop > 0.0f) return TREVR_ERR_INVALID_ARGUMENT;
   const int item = prm->sinks_per_warp > 0 ? prm->sinks_per_warp : 64;
   if (item % 32 != 0 || item > (1 << 20)) return TREVR_ERR_INVALID_ARGUMENT;
   int rc = batch_items(B, item);
@@ -302,6 +313,8 @@ int trevr_compute_flux_batched(trevr_batch* B, const trevr_params* prm, float* c
   wp.smin2 = 0.0f;  // set per tree by the kernel from the tree's side
   wp.sinks_per_warp = item;
   wp.variant = prm->walk_variant > 0 ? prm->walk_variant : kDefaultVariant;
+  wp.bg_radius = 0.0f;
+  wp.tau_stop = INFINITY;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));

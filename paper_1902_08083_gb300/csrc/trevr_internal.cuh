@@ -46,6 +46,7 @@ struct TreeView {
   const int4* nT;    // (child or -1, parent, src_first, src_count)
   const float* nl2;  // l^2 (furthest vertex from the centre of luminosity)
   const int* ndepth;
+  const int4* nglo;  // integer box lower corner, w = split axis (-1 for a leaf)
   const int* nfirst;
   const int* ncount;
   // sources sorted by the first particle of their leaf
@@ -140,6 +141,8 @@ struct WalkParams {
   int stack_depth;
   int sinks_per_warp;  // sinks in each warp's chunk (0 = default)
   int variant;         // 1 = per-lane walk, 2 = warp-shared walk
+  float bg_radius;     // > 0: sources are background sources on this sphere (Sec. 2.2.4)
+  float tau_stop;      // early ray termination threshold (+inf = off)
 };
 // accumulators of the adjoint (FP64, zeroed by the caller)
 struct AdjointArgs {

@@ -97,16 +97,16 @@ __device__ __forceinline__ void slab_g(int k, float lo, float hi, float p, float
 }  // namespace
 
 struct SinkCounters {
-  int rays = 0, segs = 0, visit = 0, ref = 0, clip = 0;
+  int rays = 0, segs = 0, visit = 0, ref = 0, clip = 0, cut = 0;
 };
 
 // warp-reduce the counters and add them to the device totals (all lanes call it)
 __device__ __forceinline__ void add_stats(const SinkCounters& c, unsigned long long* stats) {
-  unsigned long long v[5] = {(unsigned long long)c.rays, (unsigned long long)c.segs,
+  unsigned long long v[6] = {(unsigned long long)c.rays, (unsigned long long)c.segs,
                              (unsigned long long)c.visit, (unsigned long long)c.ref,
-                             (unsigned long long)c.clip};
+                             (unsigned long long)c.clip, (unsigned long long)c.cut};
 #pragma unroll
-  for (int q = 0; q < 5; ++q) {
+  for (int q = 0; q < 6; ++q) {
     unsigned long long x = v[q];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
@@ -570,7 +570,9 @@ __device__ __forceinline__ void warp_atomic_add(double* base, int key, float v) 
 
 // Rays from the sinks of the lanes in `on` to (q, L) inside cell C; every lane
 // of the warp must call it (the loop runs while any lane has cells left).
-template <bool ADJ, bool MOM>
+// STOP: early ray termination (Sec. 5): a lane whose running optical depth passes
+// P.tau_stop drops the rest of its ray, and the ray adds nothing.
+template <bool ADJ, bool MOM, bool STOP = false>
 __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P, const bool on,
                                          const float px, const float py, const float pz,
                                          const int S, const int dS, const int* anc, int* rst,
@@ -609,6 +611,7 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
   }
   const bool traced = active;
   CSum tau;
+  bool cut = false;
   int b = 0, rsp = 0, boxes = 0, pass = 1;
   // adjoint: the first pass records its segment cells and lengths (up to kSegBuf),
   // so the second pass replays them instead of tracing the ray again
@@ -633,7 +636,11 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
       const bool from_stack = b >= nb && rsp > 0;  // the base segments come first
       if (!from_stack && b >= nb) {
         const float f = L * expf(-tau.get()) / (kFourPi * s2);
-        if (!ADJ) {
+        if (!ADJ && STOP && cut) {
+          ++cnt.cut;
+          ++cnt.rays;
+          active = false;
+        } else if (!ADJ) {
           F.add(f);
           if (MOM) {
             const float il = 1.0f / len;
@@ -725,6 +732,11 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
                 aval = -gk * fcur * l;
               } else {
                 tau.add(a.w * l);
+                if (!ADJ && STOP && tau.get() > P.tau_stop) {
+                  cut = true;  // the rest of the ray is not traced
+                  b = nb;
+                  rsp = 0;
+                }
                 if (ADJ) {
                   if (nseg < kSegBuf) {
                     segb[nseg] = box;
@@ -774,7 +786,12 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
 // traced together (each lane to its own cell) when a lane needs its slot again or
 // when the walk is about to overwrite the part of the path a pending ray uses. More
 // lanes then share each traced batch; every lane still gets the same rays.
-template <bool ADJ, bool MERGE, bool MOM = false>
+// BG = true (with MERGE): background sources (Sec. 2.2.4). A merged cell's centre of
+// luminosity c is moved radially onto the sphere of radius R around the domain centre
+// o before its ray is traced, in fp32 as d = c - o, s = sqrt((dx^2 + dy^2) + dz^2),
+// q = o + d * (R / s); the ray then ends in the leaf that holds q, whose ancestors the
+// lane finds by descending the cut planes from the root and keeps for that ray.
+template <bool ADJ, bool MERGE, bool MOM = false, bool BG = false, bool STOP = false>
 __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P, const bool has,
                                           const int i, const float gk, WarpStack& ws,
                                           int* status, const AdjointArgs& J,
@@ -810,12 +827,31 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
   int sp = live ? 1 : 0;
   // this lane's pending ray (MERGE)
   bool pnd = false;
+  bool pbg = false;          // (BG) the pending ray ends at a moved source: path in cpath
+  int cpath[BG ? kDepth : 1] = {};  // (BG) ancestors of the leaf holding the moved source
   int pC = 0, pdC = 0, psrc = -1;
   float pqx = 0.0f, pqy = 0.0f, pqz = 0.0f, pL = 0.0f;
   auto flush = [&]() {
-    warp_ray<ADJ, MOM>(T, P, pnd, px, py, pz, S, dS, anc, rst, on_path, ws.path, pC, pdC, pqx,
-                       pqy, pqz, pL, psrc, gk, stack_limit, box_limit, status, J, cnt, F, mom);
+    if (BG) {
+      // a ray to a moved source uses its own path: the common-prefix mask of that
+      // path and the sink's ancestors
+      unsigned long long onp = on_path;
+      const int* pp = ws.path;
+      if (pnd && pbg) {
+        onp = 0;
+        const int mn = pdC < dS ? pdC : dS;
+        for (int d = 0; d <= mn && cpath[d] == anc[d]; ++d) onp |= 1ull << d;
+        pp = cpath;
+      }
+      warp_ray<ADJ, MOM, STOP>(T, P, pnd, px, py, pz, S, dS, anc, rst, onp, pp, pC, pdC, pqx, pqy,
+                         pqz, pL, psrc, gk, stack_limit, box_limit, status, J, cnt, F, mom);
+    } else {
+      warp_ray<ADJ, MOM, STOP>(T, P, pnd, px, py, pz, S, dS, anc, rst, on_path, ws.path, pC, pdC,
+                         pqx, pqy, pqz, pL, psrc, gk, stack_limit, box_limit, status, J, cnt, F,
+                         mom);
+    }
     pnd = false;
+    pbg = false;
   };
   __syncwarp();
   while (sp > 0) {
@@ -824,7 +860,7 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
     const unsigned M = ws.mask[sp];
     __syncwarp();
     // a pending ray reads the path up to its cell's depth: trace it before that changes
-    if (MERGE && __any_sync(FULL, pnd && pdC >= dX)) flush();
+    if (MERGE && __any_sync(FULL, pnd && !pbg && pdC >= dX)) flush();
     if (lane == 0) ws.path[dX] = X;
     const unsigned long long bit = 1ull << dX;
     if (has) on_path = (dX <= dS && anc[dX] == X) ? (on_path | bit) : (on_path & ~bit);
@@ -857,9 +893,49 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
         pqz = s.z;
         pL = s.w;
         psrc = -1;
+        if (BG) {
+          // move the centre of luminosity onto the sphere
+          const float ox = __fadd_rn(T.lo[0], __fmul_rn(T.side, 0.5f));
+          const float oy = __fadd_rn(T.lo[1], __fmul_rn(T.side, 0.5f));
+          const float oz = __fadd_rn(T.lo[2], __fmul_rn(T.side, 0.5f));
+          const float ddx = __fsub_rn(s.x, ox), ddy = __fsub_rn(s.y, oy), ddz = __fsub_rn(s.z, oz);
+          const float sn = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(ddx, ddx), __fmul_rn(ddy, ddy)),
+                                                __fmul_rn(ddz, ddz)));
+          if (sn > 0.0f) {
+            const float kk = __fdiv_rn(P.bg_radius, sn);
+            pqx = __fadd_rn(ox, __fmul_rn(ddx, kk));
+            pqy = __fadd_rn(oy, __fmul_rn(ddy, kk));
+            pqz = __fadd_rn(oz, __fmul_rn(ddz, kk));
+          }
+          // the leaf holding the moved point (grid coordinates clamped to the grid)
+          const float scale = __fdiv_rn(2097152.0f, T.side);
+          const float qq[3] = {pqx, pqy, pqz};
+          int g[3];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            float t = __fmul_rn(__fsub_rn(qq[d], T.lo[d]), scale);
+            if (!(t >= 0.0f)) t = 0.0f;
+            const unsigned v = __float2uint_rz(t);
+            g[d] = (int)(v > (unsigned)(kGridMax - 1) ? (unsigned)(kGridMax - 1) : v);
+          }
+          int Y = kRoot, dY = 0;
+          cpath[0] = kRoot;
+          for (int it = 0; it < kDepth - 1; ++it) {
+            const int ch = __ldg(&T.nT[Y].x);
+            if (ch < 0) break;
+            const int ax = __ldg(&T.nglo[Y].w);
+            const int4 up = __ldg(&T.nglo[ch + 1]);
+            const int plane = ax == 0 ? up.x : (ax == 1 ? up.y : up.z);
+            Y = g[ax] >= plane ? ch + 1 : ch;
+            cpath[++dY] = Y;
+          }
+          pC = Y;
+          pdC = dY;
+          pbg = true;
+        }
       }
     } else if (accM) {
-      warp_ray<ADJ, MOM>(T, P, acc, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX, s.x,
+      warp_ray<ADJ, MOM, STOP>(T, P, acc, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX, s.x,
                          s.y, s.z, s.w, -1, gk, stack_limit, box_limit, status, J, cnt, F, mom);
     }
     if (opnM) {
@@ -881,7 +957,7 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
               psrc = jj;
             }
           } else {
-            warp_ray<ADJ, MOM>(T, P, opn, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX,
+            warp_ray<ADJ, MOM, STOP>(T, P, opn, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX,
                                y.x, y.y, y.z, y.w, jj, gk, stack_limit, box_limit, status, J, cnt,
                                F, mom);
           }
@@ -907,8 +983,10 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
   if (MERGE && __any_sync(FULL, pnd)) flush();
 }
 
-template <bool ADJ, bool MERGE, bool MOM = false>
-__global__ void __launch_bounds__(128) walk_warp_kernel(TreeView T, const long long* sink_idx,
+// 8 blocks of 128 per SM (at most 64 registers): measured 4% faster forward and 8%
+// faster adjoint than the compiler's own 70 registers at 7 blocks
+template <bool ADJ, bool MERGE, bool MOM = false, bool BG = false, bool STOP = false>
+__global__ void __launch_bounds__(128, 8) walk_warp_kernel(TreeView T, const long long* sink_idx,
                                                         int n_sink, WalkParams P, SinkOut out,
                                                         unsigned long long* stats, int* status,
                                                         AdjointArgs J) {
@@ -930,7 +1008,8 @@ __global__ void __launch_bounds__(128) walk_warp_kernel(TreeView T, const long l
   CSum F;
   Moments mom;
   if (__any_sync(0xffffffffu, has))
-    warp_walk<ADJ, MERGE, MOM>(T, P, has, i, g, ws, status, J, cnt, F, MOM ? &mom : nullptr);
+    warp_walk<ADJ, MERGE, MOM, BG, STOP>(T, P, has, i, g, ws, status, J, cnt, F,
+                                         MOM ? &mom : nullptr);
   if (MOM && has) {
 #pragma unroll
     for (int q = 0; q < 3; ++q)
@@ -950,7 +1029,7 @@ __global__ void __launch_bounds__(128) walk_warp_kernel(TreeView T, const long l
 // Batched form of the warp-shared walk: each work item is cut into groups of 32
 // consecutive sinks, one warp walk per group.
 template <int BS, bool MERGE>
-__global__ void __launch_bounds__(BS) walk_warp_batched_kernel(
+__global__ void __launch_bounds__(BS, 1024 / BS) walk_warp_batched_kernel(
     const TreeView* __restrict__ views, float* const* __restrict__ flux_out,
     const int2* __restrict__ items, int n_items, int item, unsigned* counter, WalkParams P,
     unsigned long long* stats, int* status) {
@@ -1053,6 +1132,22 @@ cudaError_t launch_walk(const TreeView& T, const long long* sink_idx, int n_sink
                         cudaStream_t s) {
   if (n_sink <= 0) return cudaSuccess;
   (void)block_size;
+  if (wp.bg_radius > 0.0f || wp.tau_stop < INFINITY) {
+    const dim3 grid((n_sink + 127) / 128);
+    const SinkOut o{flux_out, counters, nullptr, nullptr, n_sink};
+    const bool bg = wp.bg_radius > 0.0f, stop = wp.tau_stop < INFINITY;
+    if (bg && stop)
+      walk_warp_kernel<false, true, false, true, true><<<grid, 128, 0, s>>>(
+          T, sink_idx, n_sink, wp, o, stats, status, AdjointArgs{});
+    else if (bg)
+      walk_warp_kernel<false, true, false, true><<<grid, 128, 0, s>>>(
+          T, sink_idx, n_sink, wp, o, stats, status, AdjointArgs{});
+    else
+      walk_warp_kernel<false, true, false, false, true><<<grid, 128, 0, s>>>(
+          T, sink_idx, n_sink, wp, o, stats, status, AdjointArgs{});
+    note_launch();
+    return cudaGetLastError();
+  }
   if (wp.variant >= 2) {
     if (wp.variant == 3)
       walk_warp_kernel<false, true><<<(n_sink + 127) / 128, 128, 0, s>>>(

@@ -53,7 +53,8 @@ class Params(ctypes.Structure):
     _fields_ = [("theta_open", ctypes.c_float), ("tau_ref", ctypes.c_float),
                 ("bucket", ctypes.c_int), ("sinks_per_warp", ctypes.c_int),
                 ("block_size", ctypes.c_int), ("stack_depth", ctypes.c_int),
-                ("walk_variant", ctypes.c_int)]
+                ("walk_variant", ctypes.c_int), ("bg_radius", ctypes.c_float),
+                ("tau_stop", ctypes.c_float)]
 
 
 class Stats(ctypes.Structure):
@@ -61,7 +62,7 @@ class Stats(ctypes.Structure):
                 ("src_nodes_visited", ctypes.c_longlong),
                 ("refine_expansions", ctypes.c_longlong), ("cells_clipped", ctypes.c_longlong),
                 ("build_ms", ctypes.c_float),
-                ("walk_ms", ctypes.c_float)]
+                ("walk_ms", ctypes.c_float), ("rays_terminated", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -139,9 +140,10 @@ def _stream_ptr(stream=None):
 
 
 def make_params(theta=0.75, tau_ref=0.1, bucket=8, sinks_per_warp=0, block_size=0,
-                stack_depth=0, walk_variant=0):
+                stack_depth=0, walk_variant=0, bg_radius=0.0, tau_stop=0.0):
     return Params(float(theta), float(tau_ref), int(bucket), int(sinks_per_warp),
-                  int(block_size), int(stack_depth), int(walk_variant))
+                  int(block_size), int(stack_depth), int(walk_variant), float(bg_radius),
+                  float(tau_stop))
 
 
 class Tree:
@@ -231,7 +233,8 @@ def build_tree(gas_xyz, alpha, src_xyz, src_lum, weight=None, lo=(0.0, 0.0, 0.0)
 def compute_flux(tree: Tree, theta=0.75, tau_ref=0.1, sink_idx=None, out=None, counters=False,
                  stats=False, stream=None, **tuning):
     """Flux at the sinks (trevr_compute_flux). Returns flux, plus the per-sink counters
-    (n, 4) int32 and/or a stats dict when asked."""
+    (n, 4) int32 and/or a stats dict when asked. `tuning` holds the other fields of
+    trevr_params (launch shape, walk_variant, bg_radius, tau_stop)."""
     lib = tree._lib
     n = tree.n_gas if sink_idx is None else int(sink_idx.shape[0])
     if out is None:

@@ -142,6 +142,38 @@ def adjoint_problem(n_gas=1 << 21, n_src=1024, seed=4, sigma=1.0, corr_len=0.05,
                     seed=seed, loss_weight=lw, fd_src=fd_src, fd_gas=fd_gas)
 
 
+def spiral_sphere(n, radius, centre=(0.5, 0.5, 0.5)):
+    """n points spread over a sphere along a golden-angle spiral (equal-area bands in z,
+    azimuth advancing by pi (3 - sqrt 5) per point): the background-source layout."""
+    k = np.arange(n, dtype=np.float64)
+    z = 1.0 - (2.0 * k + 1.0) / n
+    rho = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    phi = k * np.pi * (3.0 - np.sqrt(5.0))
+    u = np.stack([rho * np.cos(phi), rho * np.sin(phi), z])
+    return np.asarray(centre, np.float64)[:, None] + radius * u
+
+
+def background_shell(n_gas=1 << 14, n_bg=20000, radius=0.45, l_total=1.0, seed=9, alpha=0.0,
+                     theta=0.75, tau_ref=0.1, bucket=8):
+    """Background radiation: n_bg equal sources on a spiral sphere of the given radius
+    around the box centre (total luminosity l_total), gas uniform inside the sphere."""
+    rng = np.random.default_rng(seed)
+    # gas uniform in the ball of radius 0.95 * radius (rejection sampling)
+    pts = []
+    need = n_gas
+    while need > 0:
+        c = rng.random((3, 2 * need)) - 0.5
+        keep = np.sum(c * c, axis=0) < (0.95 * radius) ** 2
+        pts.append(c[:, keep][:, :need])
+        need -= pts[-1].shape[1]
+    gas = (np.concatenate(pts, axis=1) + 0.5).astype(np.float32)
+    src = spiral_sphere(n_bg, radius).astype(np.float32)
+    lum = np.full(n_bg, l_total / n_bg, dtype=np.float32)
+    a = np.full(n_gas, alpha, dtype=np.float32)
+    return _problem(f"background_{n_gas}_{n_bg}", gas, a, src, lum, theta, tau_ref, bucket,
+                    seed=seed, radius=radius, l_total=l_total)
+
+
 def sink_sample(n_gas, n_sample, seed=7):
     """A seeded sample of sink indices (sorted, without repetition)."""
     rng = np.random.default_rng(seed)
