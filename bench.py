@@ -346,6 +346,70 @@ def _bench_termination(args, P, g):
             "median_rel_change": float(rel.median()), "bound_holds": ok}
 
 
+def _bench_bands(args, P, g):
+    """Four bands on the workload's particles and sources (absorption x1, x1/2, x1/4, x2;
+    luminosity factors 1/2, 1/4, 1/8, 1/8): the band walk against the single-band walk
+    of band 0 (Sec. 5 expects a small constant factor)."""
+    import torch
+    from paper_1902_08083_gb300 import trevr
+    stream = torch.cuda.current_stream()
+    fa = torch.tensor([1.0, 0.5, 0.25, 2.0], device=g["alpha"].device)
+    fl = torch.tensor([0.5, 0.25, 0.125, 0.125], device=g["alpha"].device)
+    A = (fa[:, None] * g["alpha"][None, :]).contiguous()
+    L = (fl[:, None] * g["src_lum"][None, :]).contiguous()
+    kw = dict(lo=P["lo"], side=P["side"], bucket=P["bucket"])
+    tb = trevr.build_tree(g["gas_xyz"], A, g["src_xyz"], L, **kw)
+    t1 = trevr.build_tree(g["gas_xyz"], g["alpha"], g["src_xyz"], g["src_lum"], **kw)
+    Fb, st = trevr.compute_flux_bands(tb, P["theta"], P["tau_ref"], stats=True)
+    F1, st1 = trevr.compute_flux(t1, P["theta"], P["tau_ref"], stats=True)
+    multi = _time_ms(lambda: trevr.compute_flux_bands(tb, P["theta"], P["tau_ref"], out=Fb),
+                     args.steps, stream)
+    single = _time_ms(lambda: trevr.compute_flux(t1, P["theta"], P["tau_ref"], out=F1),
+                      args.steps, stream)
+    tb.free()
+    t1.free()
+    return {"workload": f"{P['gas_xyz'].shape[1]} gas, {P['src_xyz'].shape[1]} sources, "
+                        "4 bands", "walk_ms_4_bands": min(multi),
+            "walk_ms_1_band": min(single), "cost_ratio": min(multi) / min(single),
+            "segments_ratio": st["segments"] / max(st1["segments"], 1)}
+
+
+def _bench_sub_bucket(args):
+    """Sub-bucket particle trace (Sec. 2.2.3, 3.1.3) on 2^18 particles of equal volume
+    with a lognormal absorption field (sigma_ln=1.5) and 32-neighbour smoothing
+    lengths, 1024 sources: the neighbour-list build and the walk with and without
+    the trace."""
+    import torch
+    from paper_1902_08083_gb300 import trevr
+    P = workloads.sub_bucket_problem(n_gas=1 << 18, n_src=1024, seed=12)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    t = {k: torch.from_numpy(np.ascontiguousarray(P[k])).to(dev)
+         for k in ("gas_xyz", "alpha", "src_xyz", "src_lum", "weight", "hsml")}
+    tree = trevr.build_tree(t["gas_xyz"], t["alpha"], t["src_xyz"], t["src_lum"],
+                            weight=t["weight"], lo=P["lo"], side=P["side"], bucket=P["bucket"])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tree.set_smoothing(t["hsml"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    nbr_ms = e0.elapsed_time(e1)
+    F, st = trevr.compute_flux(tree, P["theta"], P["tau_ref"], sub_bucket=1, stats=True)
+    F0 = trevr.compute_flux(tree, P["theta"], P["tau_ref"])
+    sub = _time_ms(lambda: trevr.compute_flux(tree, P["theta"], P["tau_ref"], out=F,
+                                              sub_bucket=1), args.steps, stream)
+    plain = _time_ms(lambda: trevr.compute_flux(tree, P["theta"], P["tau_ref"], out=F0),
+                     args.steps, stream)
+    rel = ((F.double() - F0.double()).abs() / F0.double().clamp_min(1e-30))
+    tree.free()
+    return {"workload": f"{P['gas_xyz'].shape[1]} gas, {P['src_xyz'].shape[1]} sources, "
+                        "lognormal sigma_ln=1.5, 32-neighbour smoothing",
+            "theta": P["theta"], "tau_ref": P["tau_ref"], "neighbour_lists_ms": nbr_ms,
+            "walk_ms_sub_bucket": min(sub), "walk_ms_cell_means": min(plain),
+            "sub_bucket_segments_frac": st["sub_bucket_segments"] / max(st["segments"], 1),
+            "median_rel_change": float(rel.median())}
+
+
 def run_ours(args):
     import torch
     from paper_1902_08083_gb300 import trevr
@@ -483,6 +547,8 @@ def run_ours(args):
         line["batched"] = _bench_batched(args)
         line["adjoint"] = _bench_adjoint(args)
         line["terminated"] = _bench_termination(args, P, g)
+        line["bands"] = _bench_bands(args, P, g)
+        line["sub_bucket"] = _bench_sub_bucket(args)
 
     if world == 1 and not args.no_cpu_baseline:
         info, sinks, fo, _ = _oracle_baseline(P, n, args.cpu_sample, args.cpu_seconds)

@@ -81,6 +81,14 @@ typedef struct {
                            times its unabsorbed value). The fp32 running sum decides.
                            0 = off; negative or NaN is an invalid argument. Only
                            trevr_compute_flux accepts it. */
+    int sub_bucket;     /* 1: sub-bucket particle trace (Sec. 2.2.3, 3.1.3; needs
+                           trevr_tree_set_smoothing). A leaf whose own particles ask for
+                           refinement, (max - min of their alpha) * l > tau_ref (every
+                           leaf if tau_ref <= 0), integrates the SPH field of the
+                           particles along the ray's chord in it instead of using its
+                           mean. The receiving particle is left out of that sum. 0 = off.
+                           Only trevr_compute_flux accepts it, without bg_radius or
+                           tau_stop. */
 } trevr_params;
 
 /* Totals over the sinks of one call, and timings (ms, CUDA events). */
@@ -93,6 +101,7 @@ typedef struct {
     float build_ms;
     float walk_ms;
     long long rays_terminated;   /* rays cut off by tau_stop (of the interactions) */
+    long long sub_bucket_segments; /* leaf segments integrated through the particles */
 } trevr_stats;
 
 /*
@@ -144,6 +153,61 @@ int trevr_build_tree(const float* gas_xyz, const float* alpha, const float* weig
 int trevr_compute_flux(const trevr_tree* t, const long long* sink_idx, long long n_sink,
                        const trevr_params* prm, float* flux_out, int* sink_counters,
                        trevr_stats* stats, void* stream);
+
+/*
+ * Several bands (Sec. 5: many bands of radiation for a constant factor in cost).
+ * Band b has its own absorption coefficient per particle and its own
+ * luminosity per source. The bands share the walk and the rays. The tree, the
+ * centres of luminosity and the opening-angle test use the band-summed
+ * luminosity L_j = fp32(sum_b L_b,j), summed in FP64 in band order. Every band
+ * sums its own optical depth (Eq. tausum) over the shared segments. A cell is
+ * refined (Eq. refcrit) when any band asks for it, since its spread is
+ * max_b (alpha_max,b - alpha_min,b). One band is the plain method.
+ *
+ *   alpha_bands  n_bands x n_gas floats, band-major (band b at b * n_gas),
+ *                each >= 0 and finite.
+ *   lum_bands    n_bands x n_src floats, band-major, each >= 0 and finite.
+ *   n_bands      1 .. TREVR_MAX_BANDS.
+ *   other arguments as in trevr_build_tree (band 0's alpha is checked there).
+ * The tree holds 3 extra 16-byte records per cell and one per source. The
+ * single-band calls (trevr_compute_flux and the rest, trevr_batch_create)
+ * reject a tree with more than one band. Synchronises the stream.
+ */
+#define TREVR_MAX_BANDS 4
+int trevr_build_tree_bands(const float* gas_xyz, const float* alpha_bands, const float* weight,
+                           long long n_gas, const float* src_xyz, const float* lum_bands,
+                           long long n_src, int n_bands, const trevr_domain* dom,
+                           const trevr_params* prm, void* stream, trevr_tree** out);
+
+/*
+ * Smoothing lengths for the sub-bucket particle trace (Sec. 2.2.3, 3.1.3).
+ * Below the buckets, the absorption is the SPH field
+ * alpha(x) = sum_j alpha_j w_j W(|x - x_j|, h_j), where alpha_j w_j = kappa_j m_j
+ * is particle j's absorbing mass. W is the cubic spline with support 2h:
+ *   (1/(pi h^3)) (1 - 1.5 q^2 + 0.75 q^3)  for q = r/h < 1,
+ *   (1/(pi h^3)) (2 - q)^3 / 4            for 1 <= q < 2,
+ *   0                                     beyond.
+ * The call lists, for every leaf, the particles whose support meets its box,
+ * and keeps each leaf's alpha spread.
+ *   hsml  n_gas floats on the device, caller order, each > 0 and finite.
+ * Device memory grows by 24 B per particle, 8 B per cell and 4 B per
+ * (leaf, neighbour) pair. A second call replaces the first. A tree with more
+ * than one band is rejected. Synchronises the stream.
+ */
+int trevr_tree_set_smoothing(trevr_tree* t, const float* hsml, void* stream);
+
+/*
+ * Flux of every band at the sinks of a tree from trevr_build_tree_bands.
+ *   flux_out   n_bands x n_sink floats, band-major: band b of the k-th sink at
+ *              b * n_sink + k.
+ *   other arguments as in trevr_compute_flux. The counters and stats are those
+ *   of the shared walk. bg_radius and tau_stop must be 0. walk_variant is
+ *   ignored: the bands use the merged-ray walk.
+ * Synchronises the stream and reports device errors.
+ */
+int trevr_compute_flux_bands(const trevr_tree* t, const long long* sink_idx, long long n_sink,
+                             const trevr_params* prm, float* flux_out, int* sink_counters,
+                             trevr_stats* stats, void* stream);
 
 /*
  * The flux and its next two direction moments at the sinks (Sec. 2.1: the

@@ -79,6 +79,15 @@ def _load():
         lib.orc_flux_background.restype = ctypes.c_int
         lib.orc_flux_terminated.argtypes = [P, P, i64, f32, f32, f32, f32, P, P, ctypes.c_int]
         lib.orc_flux_terminated.restype = ctypes.c_int
+        lib.orc_build_bands.argtypes = [P, P, P, P, P, i64, P, P, P, P, i64, ctypes.c_int, P,
+                                        f32, ctypes.c_int, ctypes.POINTER(P)]
+        lib.orc_build_bands.restype = ctypes.c_int
+        lib.orc_flux_bands.argtypes = [P, P, i64, f32, f32, P, P, ctypes.c_int]
+        lib.orc_flux_bands.restype = ctypes.c_int
+        lib.orc_set_smoothing.argtypes = [P, P]
+        lib.orc_set_smoothing.restype = ctypes.c_int
+        lib.orc_flux_sub.argtypes = [P, P, i64, f32, f32, P, P, ctypes.c_int]
+        lib.orc_flux_sub.restype = ctypes.c_int
         lib.orc_sink_interactions.argtypes = [P, i64, f32, f32, f32, i64] + [P] * 8
         lib.orc_sink_interactions.restype = i64
         lib.orc_ray_tau.argtypes = [P, i64, i64, P, f32, P, P]
@@ -130,6 +139,9 @@ class OracleTree:
 
     def __init__(self, gas_xyz, alpha, src_xyz, src_lum, lo=(0.0, 0.0, 0.0), side=1.0,
                  bucket=8, weight=None):
+        """alpha (N,) and src_lum (S,); or, for several bands, alpha (B, N) and
+        src_lum (B, S) (orc_build_bands: the walk uses the band-summed luminosity and
+        refines where any band asks)."""
         lib = _load()
         self._lib = lib
         gas_xyz = _f32(gas_xyz)
@@ -144,9 +156,20 @@ class OracleTree:
         lum = _f32(src_lum)
         lo32 = _f32(lo)
         h = ctypes.c_void_p()
-        rc = lib.orc_build(_ptr(gx), _ptr(gy), _ptr(gz), _ptr(a), _ptr(w), self.n_gas, _ptr(sx),
-                           _ptr(sy), _ptr(sz), _ptr(lum), self.n_src, _ptr(lo32), float(side),
-                           int(bucket), ctypes.byref(h))
+        self.n_bands = 0
+        if a.ndim == 2:
+            self.n_bands = a.shape[0]
+            if lum.shape != (self.n_bands, self.n_src) or a.shape[1] != self.n_gas:
+                raise ValueError("alpha (B, N) and src_lum (B, S) must have the same B")
+            self._keep = self._keep + (a, lum)
+            rc = lib.orc_build_bands(_ptr(gx), _ptr(gy), _ptr(gz), _ptr(a), _ptr(w), self.n_gas,
+                                     _ptr(sx), _ptr(sy), _ptr(sz), _ptr(lum), self.n_src,
+                                     self.n_bands, _ptr(lo32), float(side), int(bucket),
+                                     ctypes.byref(h))
+        else:
+            rc = lib.orc_build(_ptr(gx), _ptr(gy), _ptr(gz), _ptr(a), _ptr(w), self.n_gas,
+                               _ptr(sx), _ptr(sy), _ptr(sz), _ptr(lum), self.n_src, _ptr(lo32),
+                               float(side), int(bucket), ctypes.byref(h))
         if rc != ORC_OK:
             raise OracleError(rc)
         self._h = h
@@ -242,6 +265,46 @@ class OracleTree:
         cnt = np.zeros((n, 4), np.int64) if with_counters else None
         rc = self._lib.orc_flux_background(self._h, _ptr(sinks), n, float(theta), float(tau_ref),
                                            float(radius), _ptr(flux), _ptr(cnt), int(nthreads))
+        if rc != ORC_OK:
+            raise OracleError(rc)
+        return (flux, cnt) if with_counters else flux
+
+    def set_smoothing(self, h):
+        """Smoothing lengths (N,) for the sub-bucket particle trace."""
+        h = _f32(h)
+        self._keep = self._keep + (h,)
+        rc = self._lib.orc_set_smoothing(self._h, _ptr(h))
+        if rc != ORC_OK:
+            raise OracleError(rc)
+
+    def flux_sub(self, theta, tau_ref, sinks=None, nthreads=0, with_counters=False):
+        """Flux with the sub-bucket particle trace: a bucket whose alpha spread times the
+        chord exceeds tau_ref (every bucket if tau_ref <= 0) integrates the SPH field
+        of the particles along the chord, leaving out the receiving particle. counters
+        columns: those of flux(), then the sub-bucket segments."""
+        if sinks is None:
+            sinks = np.arange(self.n_gas, dtype=np.int64)
+        sinks = np.ascontiguousarray(sinks, dtype=np.int64)
+        n = sinks.shape[0]
+        flux = np.zeros(n)
+        cnt = np.zeros((n, 5), np.int64) if with_counters else None
+        rc = self._lib.orc_flux_sub(self._h, _ptr(sinks), n, float(theta), float(tau_ref),
+                                    _ptr(flux), _ptr(cnt), int(nthreads))
+        if rc != ORC_OK:
+            raise OracleError(rc)
+        return (flux, cnt) if with_counters else flux
+
+    def flux_bands(self, theta, tau_ref, sinks=None, nthreads=0, with_counters=False):
+        """Flux of every band (tree built with alpha (B, N)), shape (B, n); counters as
+        in flux()."""
+        if sinks is None:
+            sinks = np.arange(self.n_gas, dtype=np.int64)
+        sinks = np.ascontiguousarray(sinks, dtype=np.int64)
+        n = sinks.shape[0]
+        flux = np.zeros((max(self.n_bands, 1), n))
+        cnt = np.zeros((n, 4), np.int64) if with_counters else None
+        rc = self._lib.orc_flux_bands(self._h, _ptr(sinks), n, float(theta), float(tau_ref),
+                                      _ptr(flux), _ptr(cnt), int(nthreads))
         if rc != ORC_OK:
             raise OracleError(rc)
         return (flux, cnt) if with_counters else flux

@@ -77,7 +77,19 @@ typedef struct {
     /* sources, sorted by (first particle of their leaf, caller index) */
     int64_t *src_order, *src_leaf;
     float *sx, *sy, *sz, *slum;
+
+    /* several bands (orc_build_bands; nb = 0 otherwise): per cell and band the mean
+       absorption and the luminosity, per sorted source and band the luminosity */
+    int nb;
+    double *babar, *bL;
+    float *bslum;
+
+    /* smoothing lengths (orc_set_smoothing; NULL otherwise): per sorted particle,
+       and per leaf the spread max - min of its particles' alpha (fp32) */
+    float *hsml, *dbk;
 } orc_tree;
+
+#define ORC_MAXB 8
 
 /* ------------------------------------------------------------------------ */
 /* Morton key: q_d = floor((x_d - lo_d) * (2^21/side)), clamped to 2^21-1,    */
@@ -498,6 +510,82 @@ nomem:
     return ORC_ERR_NO_MEMORY;
 }
 
+/*
+ * Several bands (Sec. 5: many bands for a constant factor in cost). Band b has its
+ * own absorption alpha_b (band-major, n_bands x n_gas) and its own source
+ * luminosities L_b (n_bands x n_src). Reading: the walk and the rays are shared
+ * by the bands. The tree, the centres of luminosity and the opening-angle test
+ * use the summed luminosity L = sum_b L_b (FP64 in band order, rounded to fp32
+ * per source). Each band keeps its own optical depth along the shared segments.
+ * A cell is refined when any band asks for it: the refinement test uses
+ * max_b (alpha_max,b - alpha_min,b). With one band this is the plain method.
+ */
+int orc_build_bands(const float *gas_x, const float *gas_y, const float *gas_z,
+                    const float *alpha_bands, const float *weight, int64_t n_gas,
+                    const float *src_x, const float *src_y, const float *src_z,
+                    const float *lum_bands, int64_t n_src, int n_bands, const float lo[3],
+                    float side, int bucket, orc_tree **out)
+{
+    *out = NULL;
+    if (n_bands < 1 || n_bands > ORC_MAXB || n_gas <= 0 || n_src < 0)
+        return ORC_ERR_INVALID_ARGUMENT;
+    for (int64_t k = 0; k < (int64_t)n_bands * n_gas; ++k)
+        if (!isfinite(alpha_bands[k]) || alpha_bands[k] < 0.0f) return ORC_ERR_INVALID_ARGUMENT;
+    for (int64_t k = 0; k < (int64_t)n_bands * n_src; ++k)
+        if (!isfinite(lum_bands[k]) || lum_bands[k] < 0.0f) return ORC_ERR_INVALID_ARGUMENT;
+    float *lsum = malloc((size_t)(n_src > 0 ? n_src : 1) * sizeof(float));
+    if (!lsum) return ORC_ERR_NO_MEMORY;
+    for (int64_t j = 0; j < n_src; ++j) {
+        double t = 0.0;
+        for (int b = 0; b < n_bands; ++b) t += (double)lum_bands[(int64_t)b * n_src + j];
+        lsum[j] = (float)t;
+    }
+    orc_tree *T = NULL;
+    int rc = orc_build(gas_x, gas_y, gas_z, alpha_bands, weight, n_gas, src_x, src_y, src_z,
+                       lsum, n_src, lo, side, bucket, &T);
+    free(lsum);
+    if (rc != ORC_OK) return rc;
+    const int64_t nn = T->n_nodes, B = n_bands;
+    double *dmax = calloc((size_t)nn, sizeof(double));
+    T->nb = n_bands;
+    T->babar = calloc((size_t)(nn * B), sizeof(double));
+    T->bL = calloc((size_t)(nn * B), sizeof(double));
+    T->bslum = calloc((size_t)(n_src > 0 ? n_src * B : 1), sizeof(float));
+    if (!dmax || !T->babar || !T->bL || !T->bslum) {
+        free(dmax);
+        orc_tree_free(T);
+        return ORC_ERR_NO_MEMORY;
+    }
+    for (int64_t s = 0; s < n_src; ++s)
+        for (int64_t b = 0; b < B; ++b)
+            T->bslum[s * B + b] = lum_bands[b * n_src + T->src_order[s]];
+    for (int64_t b = 0; b < B; ++b) {
+        /* this band's absorption: mean and directional spread of every cell */
+        for (int64_t i = 0; i < n_gas; ++i) T->alpha[i] = alpha_bands[b * n_gas + T->perm[i]];
+        node_moments(T);
+        for (int64_t X = 0; X < nn; ++X) {
+            T->babar[X * B + b] = T->abar[X];
+            const double d = T->amax[X] - T->amin[X];
+            if (b == 0 || d > dmax[X]) dmax[X] = d;
+            double sl = 0.0;
+            for (int64_t s = T->src_first[X]; s < T->src_first[X] + T->src_count[X]; ++s)
+                sl += (double)T->bslum[s * B + b];
+            T->bL[X * B + b] = sl;
+        }
+    }
+    /* band 0 in the single-band fields; the refinement test takes the largest spread */
+    for (int64_t i = 0; i < n_gas; ++i) T->alpha[i] = alpha_bands[T->perm[i]];
+    node_moments(T);
+    for (int64_t X = 0; X < nn; ++X) {
+        T->amin[X] = 0.0;
+        T->amax[X] = dmax[X];
+        T->dalpha32[X] = (float)dmax[X];
+    }
+    free(dmax);
+    *out = T;
+    return ORC_OK;
+}
+
 void orc_tree_free(orc_tree *T)
 {
     if (!T) return;
@@ -506,7 +594,7 @@ void orc_tree_free(orc_tree *T)
                     T->glo, T->ghi, T->W, T->abar, T->amin_d, T->amax_d, T->amin, T->amax, T->L,
                     T->cen, T->lrad, T->abar32, T->dalpha32, T->L32, T->cen32, T->l2_32, T->blo32,
                     T->bhi32, T->src_first, T->src_count, T->src_order, T->src_leaf, T->sx, T->sy,
-                    T->sz, T->slum};
+                    T->sz, T->slum, T->babar, T->bL, T->bslum, T->hsml, T->dbk};
     for (size_t k = 0; k < sizeof(ptrs) / sizeof(ptrs[0]); ++k) free(ptrs[k]);
     free(T);
 }
@@ -596,6 +684,9 @@ typedef struct {
     float p[3], d[3], inv[3], len;
     /* FP64 ray for the values */
     double P[3], D[3], LEN;
+    /* the receiving particle (sorted index) and the sub-bucket switch */
+    int64_t sink;
+    int sub;
 } ray_t;
 
 typedef struct {
@@ -612,7 +703,7 @@ static void nsum_add(nsum_t *s, double x)
 static double nsum_get(const nsum_t *s) { return s->sum + s->comp; }
 
 typedef struct {
-    int64_t interactions, segments, visited, refinements, terminated;
+    int64_t interactions, segments, visited, refinements, terminated, subbucket;
     double margin;
     /* optional record of the frozen decisions */
     int record;
@@ -662,10 +753,122 @@ static double clip64(const orc_tree *T, const ray_t *R, int64_t X)
     return t1 > t0 ? (t1 - t0) * R->LEN : 0.0;
 }
 
+/* FP64 parameter range [t0, t1] of the ray inside the node box (as clip64). */
+static void clip64_range(const orc_tree *T, const ray_t *R, int64_t X, double *t0o, double *t1o)
+{
+    double t0 = 0.0, t1 = 1.0;
+    for (int k = 0; k < 3; ++k) {
+        double lo = T->lo[k] + (double)T->glo[X][k] * T->h;
+        double hi = T->lo[k] + (double)T->ghi[X][k] * T->h;
+        if (R->D[k] != 0.0) {
+            double ta = (lo - R->P[k]) / R->D[k];
+            double tb = (hi - R->P[k]) / R->D[k];
+            t0 = fmax(t0, fmin(ta, tb));
+            t1 = fmin(t1, fmax(ta, tb));
+        } else if (R->P[k] < lo || R->P[k] >= hi) {
+            t1 = t0;
+        }
+    }
+    *t0o = t0;
+    *t1o = t1 > t0 ? t1 : t0;
+}
+
+/*
+ * Sub-bucket particle trace (Sec. 2.2.3, 3.1.3). The absorption below the bucket
+ * scale is the SPH field alpha(x) = sum_j alpha_j w_j W(|x - x_j|, h_j): alpha_j w_j
+ * = kappa_j m_j is particle j's absorbing mass, and W is the cubic spline
+ * W(r, h) = (1/(pi h^3)) (1 - 3/2 q^2 + 3/4 q^3) for q = r/h < 1,
+ * (1/(pi h^3)) (2 - q)^3 / 4 for 1 <= q < 2, and 0 beyond. Along a ray at impact
+ * parameter b from x_j, r = sqrt(b^2 + s^2). The integral over s uses closed-form
+ * antiderivatives of r^n (the integral of r^n du from 0 to s):
+ *   n = 0: s
+ *   n = 1: (s r + b^2 ln((s + r)/b)) / 2
+ *   n = 2: b^2 s + s^3 / 3
+ *   n = 3: s r^3 / 4 + 3 b^2 s r / 8 + 3 b^4 ln((s + r)/b) / 8
+ */
+static double rpow_int(int n, double b, double s)
+{
+    const double r = sqrt(b * b + s * s);
+    const double lg = b > 0.0 ? log((s + r) / b) : 0.0;
+    switch (n) {
+    case 0: return s;
+    case 1: return 0.5 * (s * r + b * b * lg);
+    case 2: return b * b * s + s * s * s / 3.0;
+    default: return s * r * r * r / 4.0 + 3.0 * b * b * s * r / 8.0 + 3.0 * b * b * b * b * lg / 8.0;
+    }
+}
+
+/* integral of W(sqrt(b^2 + u^2), h) du over [0, s], s >= 0 */
+static double kernel_half_line(double b, double s, double h)
+{
+    const double u1 = b < h ? sqrt(h * h - b * b) : 0.0;         /* r = h */
+    const double u2 = b < 2.0 * h ? sqrt(4.0 * h * h - b * b) : 0.0; /* r = 2h */
+    const double a1 = fmin(s, u1), a2 = fmin(s, u2);
+    double in = 0.0, out = 0.0;
+    if (a1 > 0.0)
+        in = rpow_int(0, b, a1) - 1.5 / (h * h) * rpow_int(2, b, a1) +
+             0.75 / (h * h * h) * rpow_int(3, b, a1);
+    if (a2 > a1)
+        out = 2.0 * (rpow_int(0, b, a2) - rpow_int(0, b, a1)) -
+              3.0 / h * (rpow_int(1, b, a2) - rpow_int(1, b, a1)) +
+              1.5 / (h * h) * (rpow_int(2, b, a2) - rpow_int(2, b, a1)) -
+              0.25 / (h * h * h) * (rpow_int(3, b, a2) - rpow_int(3, b, a1));
+    return (in + out) / (M_PI * h * h * h);
+}
+
+/* integral of W along the line from s0 to s1 (s measured from the closest approach) */
+static double kernel_line(double b, double s0, double s1, double h)
+{
+    const double g1 = s1 >= 0.0 ? kernel_half_line(b, s1, h) : -kernel_half_line(b, -s1, h);
+    const double g0 = s0 >= 0.0 ? kernel_half_line(b, s0, h) : -kernel_half_line(b, -s0, h);
+    return g1 - g0;
+}
+
+/* optical depth of the chord t in [t0, t1] of the ray through the SPH field, the
+   receiving particle R->sink left out (it does not shadow itself) */
+static double sph_chord(const orc_tree *T, const ray_t *R, double t0, double t1)
+{
+    if (!(t1 > t0)) return 0.0;
+    const double D2 = R->D[0] * R->D[0] + R->D[1] * R->D[1] + R->D[2] * R->D[2];
+    double lo[3], hi[3];
+    for (int k = 0; k < 3; ++k) {
+        const double e0 = R->P[k] + t0 * R->D[k], e1 = R->P[k] + t1 * R->D[k];
+        lo[k] = fmin(e0, e1);
+        hi[k] = fmax(e0, e1);
+    }
+    nsum_t tau = {0.0, 0.0};
+    for (int64_t j = 0; j < T->n_gas; ++j) {
+        if (j == R->sink) continue;
+        const double a = (double)T->alpha[j] * (double)T->w[j];
+        if (!(a > 0.0)) continue;
+        const double H = (double)T->hsml[j];
+        const double x[3] = {T->px[j], T->py[j], T->pz[j]};
+        double g2 = 0.0; /* squared distance from x_j to the chord's bounding box */
+        for (int k = 0; k < 3; ++k) {
+            const double e = fmax(fmax(lo[k] - x[k], x[k] - hi[k]), 0.0);
+            g2 += e * e;
+        }
+        if (g2 >= 4.0 * H * H) continue;
+        double ud = 0.0;
+        for (int k = 0; k < 3; ++k) ud += (x[k] - R->P[k]) * R->D[k];
+        const double tc = ud / D2;
+        double b2 = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            const double e = x[k] - (R->P[k] + tc * R->D[k]);
+            b2 += e * e;
+        }
+        if (b2 >= 4.0 * H * H) continue;
+        const double L = sqrt(D2);
+        nsum_add(&tau, a * kernel_line(sqrt(b2), (t0 - tc) * L, (t1 - tc) * L, H));
+    }
+    return nsum_get(&tau);
+}
+
 typedef struct {
     nsum_t tau;
     double len_sum; /* sum of the FP64 lengths of the used segments (tiling check) */
     int64_t nseg;
+    nsum_t taub[ORC_MAXB]; /* optical depth of each band (trees with bands) */
 } raysum_t;
 
 /* Optical depth through node X: use its mean absorption unless the
@@ -675,6 +878,17 @@ static void seg(const orc_tree *T, const ray_t *R, int64_t X, float tau_ref, cou
 {
     float l32 = clip32(R, T->blo32[X], T->bhi32[X]);
     if (!(l32 > 0.0f)) return;
+    if (R->sub && T->split_bit[X] < 0 && (tau_ref <= 0.0f || T->dbk[X] * l32 > tau_ref)) {
+        /* a bucket that still asks for refinement: trace its particles */
+        double t0, t1;
+        clip64_range(T, R, X, &t0, &t1);
+        nsum_add(&rs->tau, sph_chord(T, R, t0, t1));
+        rs->len_sum += (t1 - t0) * R->LEN;
+        rs->nseg++;
+        c->segments++;
+        c->subbucket++;
+        return;
+    }
     if (T->split_bit[X] >= 0) {
         int refine = (tau_ref <= 0.0f) || (T->dalpha32[X] * l32 > tau_ref);
         if (tau_ref > 0.0f) {
@@ -690,6 +904,7 @@ static void seg(const orc_tree *T, const ray_t *R, int64_t X, float tau_ref, cou
     }
     double l64 = clip64(T, R, X);
     nsum_add(&rs->tau, T->abar[X] * l64);
+    for (int b = 0; b < T->nb; ++b) nsum_add(&rs->taub[b], T->babar[X * T->nb + b] * l64);
     rs->len_sum += l64;
     rs->nseg++;
     c->segments++;
@@ -754,32 +969,34 @@ typedef struct {
     nsum_t v[9];
 } moments_t;
 
-static moments_t *g_no_moments = NULL;
+/* Options of one walk beyond theta and tau_ref (all off when zero). */
+typedef struct {
+    float bg_radius;  /* > 0: background sources on this sphere (Sec. 2.2.4) */
+    float tau_stop;   /* > 0: early ray termination (Sec. 5) */
+    int sub_bucket;   /* particle trace below the buckets (Sec. 2.2.3, 3.1.3) */
+    nsum_t *bandF;    /* per-band flux accumulators (trees with bands) */
+} walkopt_t;
 
-/* One pseudo-source (L at q, inside node C) seen from sorted particle i. */
-static double contribute_m(const orc_tree *T, int64_t i, int64_t S, int64_t C, const float q32[3],
-                           const double q64[3], double L, float tau_ref, float smin2,
-                           counters_t *c, inter_log_t *log, int64_t src, moments_t *mom,
-                           float tau_stop);
+static const walkopt_t NO_OPTS = {0.0f, 0.0f, 0, NULL};
 
-static double contribute(const orc_tree *T, int64_t i, int64_t S, int64_t C, const float q32[3],
-                         const double q64[3], double L, float tau_ref, float smin2,
-                         counters_t *c, inter_log_t *log, int64_t src)
-{
-    return contribute_m(T, i, S, C, q32, q64, L, tau_ref, smin2, c, log, src, g_no_moments,
-                        0.0f);
-}
-
-/* tau_stop > 0: early ray termination (Sec. 5, proposed there). The optical depth
+/* One pseudo-source (L at q, inside node C) seen from sorted particle i.
+   tau_stop > 0: early ray termination (Sec. 5, proposed there). The optical depth
    sum of a ray is abandoned once it passes tau_stop, and the ray then adds nothing.
    Every term of the sum is non-negative, so a partial sum passes tau_stop exactly
-   when the complete sum does: here the complete sum decides. */
+   when the complete sum does: here the complete sum decides.
+   bandF (trees with bands): each band's flux L_b exp(-tau_b) / (4 pi s^2) is added to
+   bandF[b], L_b the band luminosity of the source (src >= 0) or of the merged cell C. */
 static double contribute_m(const orc_tree *T, int64_t i, int64_t S, int64_t C, const float q32[3],
                            const double q64[3], double L, float tau_ref, float smin2,
                            counters_t *c, inter_log_t *log, int64_t src, moments_t *mom,
-                           float tau_stop)
+                           const walkopt_t *o)
 {
+    const float tau_stop = o->tau_stop;
+    nsum_t *bandF = o->bandF;
     ray_t R;
+    memset(&R, 0, sizeof(R));
+    R.sink = i;
+    R.sub = o->sub_bucket;
     R.p[0] = T->px[i];
     R.p[1] = T->py[i];
     R.p[2] = T->pz[i];
@@ -803,6 +1020,12 @@ static double contribute_m(const orc_tree *T, int64_t i, int64_t S, int64_t C, c
     double f = cut ? 0.0 : L * exp(-tau) / (4.0 * M_PI * S2);
     c->interactions++;
     c->terminated += cut;
+    if (bandF) {
+        for (int b = 0; b < T->nb; ++b) {
+            const double Lb = src >= 0 ? (double)T->bslum[src * T->nb + b] : T->bL[C * T->nb + b];
+            nsum_add(&bandF[b], Lb * exp(-nsum_get(&rs.taub[b])) / (4.0 * M_PI * S2));
+        }
+    }
     if (mom) {
         const double n[3] = {-R.D[0] / R.LEN, -R.D[1] / R.LEN, -R.D[2] / R.LEN};
         for (int k = 0; k < 3; ++k) nsum_add(&mom->v[k], f * n[k]);
@@ -836,13 +1059,12 @@ static double contribute_m(const orc_tree *T, int64_t i, int64_t S, int64_t C, c
  * by one.  fp32 decision: l^2 < theta^2 r^2.
  */
 static double sink_flux_m(const orc_tree *T, int64_t i, float theta, float tau_ref,
-                          counters_t *c, inter_log_t *log, moments_t *mom, float bg_radius,
-                          float tau_stop);
+                          counters_t *c, inter_log_t *log, moments_t *mom, const walkopt_t *o);
 
 static double sink_flux(const orc_tree *T, int64_t i, float theta, float tau_ref,
                         counters_t *c, inter_log_t *log)
 {
-    return sink_flux_m(T, i, theta, tau_ref, c, log, NULL, 0.0f, 0.0f);
+    return sink_flux_m(T, i, theta, tau_ref, c, log, NULL, &NO_OPTS);
 }
 
 /* Leaf holding a point that may sit a rounding step outside the domain: its grid
@@ -889,9 +1111,9 @@ static void bg_project(const orc_tree *T, const float c32[3], const double c64[3
 }
 
 static double sink_flux_m(const orc_tree *T, int64_t i, float theta, float tau_ref,
-                          counters_t *c, inter_log_t *log, moments_t *mom, float bg_radius,
-                          float tau_stop)
+                          counters_t *c, inter_log_t *log, moments_t *mom, const walkopt_t *o)
 {
+    const float bg_radius = o->bg_radius;
     const float theta2 = theta * theta;
     const float smin = 1e-12f * T->side32;
     const float smin2 = smin * smin;
@@ -927,17 +1149,17 @@ static double sink_flux_m(const orc_tree *T, int64_t i, float theta, float tau_r
             bg_project(T, T->cen32[X], T->cen[X], bg_radius, q32, q64);
             const int64_t Cq = leaf_of_point_clamped(T, q32);
             nsum_add(&F, contribute_m(T, i, S, Cq, q32, q64, T->L[X], tau_ref, smin2, c, log, -1,
-                                      mom, tau_stop));
+                                      mom, o));
         } else if (accept) {
             nsum_add(&F, contribute_m(T, i, S, X, T->cen32[X], T->cen[X], T->L[X], tau_ref, smin2,
-                                      c, log, -1, mom, tau_stop));
+                                      c, log, -1, mom, o));
         } else if (T->split_bit[X] < 0) {
             for (int64_t s = T->src_first[X]; s < T->src_first[X] + T->src_count[X]; ++s) {
                 if (!(T->slum[s] > 0.0f)) continue;
                 const float q32[3] = {T->sx[s], T->sy[s], T->sz[s]};
                 const double q64[3] = {(double)T->sx[s], (double)T->sy[s], (double)T->sz[s]};
                 nsum_add(&F, contribute_m(T, i, S, X, q32, q64, (double)T->slum[s], tau_ref, smin2,
-                                          c, log, s, mom, tau_stop));
+                                          c, log, s, mom, o));
             }
         } else {
             stack[sp++] = T->upper[X];
@@ -956,6 +1178,7 @@ static double sink_flux_m(const orc_tree *T, int64_t i, float theta, float tau_r
 int orc_flux(const orc_tree *T, const int64_t *sinks, int64_t n_sink, float theta, float tau_ref,
              double *flux, int64_t *counters, double *margin, int nthreads)
 {
+    if (T->nb > 1) return ORC_ERR_INVALID_ARGUMENT; /* a tree with bands: orc_flux_bands */
     if (!(theta >= 0.0f) || !isfinite(theta) || isnan(tau_ref)) return ORC_ERR_INVALID_ARGUMENT;
     for (int64_t k = 0; k < n_sink; ++k)
         if (sinks[k] < 0 || sinks[k] >= T->n_gas) return ORC_ERR_INVALID_ARGUMENT;
@@ -988,6 +1211,7 @@ int orc_flux(const orc_tree *T, const int64_t *sinks, int64_t n_sink, float thet
 int orc_flux_moments(const orc_tree *T, const int64_t *sinks, int64_t n_sink, float theta,
                      float tau_ref, double *flux, double *fvec, double *press, int nthreads)
 {
+    if (T->nb > 1) return ORC_ERR_INVALID_ARGUMENT; /* a tree with bands: orc_flux_bands */
     if (!(theta >= 0.0f) || !isfinite(theta) || isnan(tau_ref)) return ORC_ERR_INVALID_ARGUMENT;
     for (int64_t k = 0; k < n_sink; ++k)
         if (sinks[k] < 0 || sinks[k] >= T->n_gas) return ORC_ERR_INVALID_ARGUMENT;
@@ -1001,7 +1225,7 @@ int orc_flux_moments(const orc_tree *T, const int64_t *sinks, int64_t n_sink, fl
         c.margin = INFINITY;
         moments_t m;
         memset(&m, 0, sizeof(m));
-        flux[k] = sink_flux_m(T, T->rank[sinks[k]], theta, tau_ref, &c, NULL, &m, 0.0f, 0.0f);
+        flux[k] = sink_flux_m(T, T->rank[sinks[k]], theta, tau_ref, &c, NULL, &m, &NO_OPTS);
         for (int q = 0; q < 3; ++q)
             if (fvec) fvec[3 * k + q] = nsum_get(&m.v[q]);
         for (int q = 0; q < 6; ++q)
@@ -1016,6 +1240,7 @@ int orc_flux_background(const orc_tree *T, const int64_t *sinks, int64_t n_sink,
                         float tau_ref, float bg_radius, double *flux, int64_t *counters,
                         int nthreads)
 {
+    if (T->nb > 1) return ORC_ERR_INVALID_ARGUMENT; /* a tree with bands: orc_flux_bands */
     if (!(theta >= 0.0f) || !isfinite(theta) || isnan(tau_ref) || !(bg_radius > 0.0f))
         return ORC_ERR_INVALID_ARGUMENT;
     for (int64_t k = 0; k < n_sink; ++k)
@@ -1028,8 +1253,8 @@ int orc_flux_background(const orc_tree *T, const int64_t *sinks, int64_t n_sink,
         counters_t c;
         memset(&c, 0, sizeof(c));
         c.margin = INFINITY;
-        flux[k] = sink_flux_m(T, T->rank[sinks[k]], theta, tau_ref, &c, NULL, NULL, bg_radius,
-                              0.0f);
+        const walkopt_t o = {bg_radius, 0.0f, 0, NULL};
+        flux[k] = sink_flux_m(T, T->rank[sinks[k]], theta, tau_ref, &c, NULL, NULL, &o);
         if (counters) {
             counters[4 * k + 0] = c.interactions;
             counters[4 * k + 1] = c.segments;
@@ -1049,6 +1274,7 @@ int orc_flux_terminated(const orc_tree *T, const int64_t *sinks, int64_t n_sink,
                         float tau_ref, float tau_stop, float bg_radius, double *flux,
                         int64_t *counters, int nthreads)
 {
+    if (T->nb > 1) return ORC_ERR_INVALID_ARGUMENT; /* a tree with bands: orc_flux_bands */
     if (!(theta >= 0.0f) || !isfinite(theta) || isnan(tau_ref) || !(tau_stop > 0.0f) ||
         !(bg_radius >= 0.0f))
         return ORC_ERR_INVALID_ARGUMENT;
@@ -1062,14 +1288,101 @@ int orc_flux_terminated(const orc_tree *T, const int64_t *sinks, int64_t n_sink,
         counters_t c;
         memset(&c, 0, sizeof(c));
         c.margin = INFINITY;
-        flux[k] = sink_flux_m(T, T->rank[sinks[k]], theta, tau_ref, &c, NULL, NULL, bg_radius,
-                              tau_stop);
+        const walkopt_t o = {bg_radius, tau_stop, 0, NULL};
+        flux[k] = sink_flux_m(T, T->rank[sinks[k]], theta, tau_ref, &c, NULL, NULL, &o);
         if (counters) {
             counters[5 * k + 0] = c.interactions;
             counters[5 * k + 1] = c.segments;
             counters[5 * k + 2] = c.visited;
             counters[5 * k + 3] = c.refinements;
             counters[5 * k + 4] = c.terminated;
+        }
+    }
+    return ORC_OK;
+}
+
+/* Flux of every band of a tree built by orc_build_bands: flux[b * n_sink + k].
+   counters (nullable): 4 int64 per sink as in orc_flux. */
+int orc_flux_bands(const orc_tree *T, const int64_t *sinks, int64_t n_sink, float theta,
+                   float tau_ref, double *flux, int64_t *counters, int nthreads)
+{
+    if (T->nb < 1 || !(theta >= 0.0f) || !isfinite(theta) || isnan(tau_ref))
+        return ORC_ERR_INVALID_ARGUMENT;
+    for (int64_t k = 0; k < n_sink; ++k)
+        if (sinks[k] < 0 || sinks[k] >= T->n_gas) return ORC_ERR_INVALID_ARGUMENT;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t k = 0; k < n_sink; ++k) {
+        counters_t c;
+        memset(&c, 0, sizeof(c));
+        c.margin = INFINITY;
+        nsum_t F[ORC_MAXB];
+        memset(F, 0, sizeof(F));
+        const walkopt_t o = {0.0f, 0.0f, 0, F};
+        sink_flux_m(T, T->rank[sinks[k]], theta, tau_ref, &c, NULL, NULL, &o);
+        for (int b = 0; b < T->nb; ++b) flux[(int64_t)b * n_sink + k] = nsum_get(&F[b]);
+        if (counters) {
+            counters[4 * k + 0] = c.interactions;
+            counters[4 * k + 1] = c.segments;
+            counters[4 * k + 2] = c.visited;
+            counters[4 * k + 3] = c.refinements;
+        }
+    }
+    return ORC_OK;
+}
+
+/* Smoothing lengths h (n_gas, caller order, > 0) for the sub-bucket trace; also
+   the spread max - min of alpha over each bucket's particles, the sub-bucket
+   refinement test's alpha_max - alpha_min (fp32). */
+int orc_set_smoothing(orc_tree *T, const float *h)
+{
+    if (T->nb > 1) return ORC_ERR_INVALID_ARGUMENT;
+    for (int64_t i = 0; i < T->n_gas; ++i)
+        if (!(h[i] > 0.0f) || !isfinite(h[i])) return ORC_ERR_INVALID_ARGUMENT;
+    if (!T->hsml) T->hsml = calloc((size_t)T->n_gas, sizeof(float));
+    if (!T->dbk) T->dbk = calloc((size_t)T->n_nodes, sizeof(float));
+    if (!T->hsml || !T->dbk) return ORC_ERR_NO_MEMORY;
+    for (int64_t i = 0; i < T->n_gas; ++i) T->hsml[i] = h[T->perm[i]];
+    for (int64_t X = 0; X < T->n_nodes; ++X) {
+        T->dbk[X] = 0.0f;
+        if (T->split_bit[X] >= 0) continue;
+        float mn = INFINITY, mx = -INFINITY;
+        for (int64_t i = T->first[X]; i < T->first[X] + T->count[X]; ++i) {
+            mn = fminf(mn, T->alpha[i]);
+            mx = fmaxf(mx, T->alpha[i]);
+        }
+        T->dbk[X] = mx - mn;
+    }
+    return ORC_OK;
+}
+
+/* Flux with the sub-bucket particle trace (needs orc_set_smoothing). counters
+   (nullable): 5 int64 per sink, those of orc_flux and the sub-bucket segments. */
+int orc_flux_sub(const orc_tree *T, const int64_t *sinks, int64_t n_sink, float theta,
+                 float tau_ref, double *flux, int64_t *counters, int nthreads)
+{
+    if (T->nb > 1 || !T->hsml || !(theta >= 0.0f) || !isfinite(theta) || isnan(tau_ref))
+        return ORC_ERR_INVALID_ARGUMENT;
+    for (int64_t k = 0; k < n_sink; ++k)
+        if (sinks[k] < 0 || sinks[k] >= T->n_gas) return ORC_ERR_INVALID_ARGUMENT;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+    for (int64_t k = 0; k < n_sink; ++k) {
+        counters_t c;
+        memset(&c, 0, sizeof(c));
+        c.margin = INFINITY;
+        const walkopt_t o = {0.0f, 0.0f, 1, NULL};
+        flux[k] = sink_flux_m(T, T->rank[sinks[k]], theta, tau_ref, &c, NULL, NULL, &o);
+        if (counters) {
+            counters[5 * k + 0] = c.interactions;
+            counters[5 * k + 1] = c.segments;
+            counters[5 * k + 2] = c.visited;
+            counters[5 * k + 3] = c.refinements;
+            counters[5 * k + 4] = c.subbucket;
         }
     }
     return ORC_OK;
@@ -1090,7 +1403,8 @@ int64_t orc_sink_interactions(const orc_tree *T, int64_t sink, float theta, floa
     counters_t c;
     memset(&c, 0, sizeof(c));
     c.margin = INFINITY;
-    sink_flux_m(T, T->rank[sink], theta, tau_ref, &c, &log, NULL, bg_radius, 0.0f);
+    const walkopt_t o = {bg_radius, 0.0f, 0, NULL};
+    sink_flux_m(T, T->rank[sink], theta, tau_ref, &c, &log, NULL, &o);
     for (int64_t k = 0; k < log.n && k < cap; ++k) {
         const inter_t *e = &log.buf[k];
         if (node) node[k] = e->node;
@@ -1114,6 +1428,7 @@ double orc_ray_tau(const orc_tree *T, int64_t sink, int64_t C, const float q[3],
 {
     int64_t i = T->rank[sink];
     ray_t R;
+    memset(&R, 0, sizeof(R));
     R.p[0] = T->px[i];
     R.p[1] = T->py[i];
     R.p[2] = T->pz[i];
@@ -1254,6 +1569,8 @@ static void ray_segments(const orc_tree *T, const ray_t *R, int64_t S, int64_t C
 
 static void make_ray(const orc_tree *T, int64_t i, const float q32[3], const double q64[3], ray_t *R)
 {
+    memset(R, 0, sizeof(*R));
+    R->sink = i;
     R->p[0] = T->px[i];
     R->p[1] = T->py[i];
     R->p[2] = T->pz[i];
@@ -1355,6 +1672,7 @@ static void adj_sink(const orc_tree *T, int64_t i, float theta, float tau_ref, d
 int orc_adjoint(const orc_tree *T, const int64_t *sinks, int64_t n_sink, const double *grad_flux,
                 float theta, float tau_ref, double *grad_lum, double *grad_alpha, int nthreads)
 {
+    if (T->nb > 1) return ORC_ERR_INVALID_ARGUMENT; /* a tree with bands: orc_flux_bands */
     for (int64_t k = 0; k < n_sink; ++k)
         if (sinks[k] < 0 || sinks[k] >= T->n_gas) return ORC_ERR_INVALID_ARGUMENT;
     const int64_t nn = T->n_nodes;
@@ -1461,6 +1779,7 @@ static void rec_interaction(const orc_tree *T, int64_t i, int64_t S, int64_t C, 
 int orc_replay_record(const orc_tree *T, const int64_t *sinks, int64_t n_sink, float theta,
                       float tau_ref, orc_replay **out)
 {
+    if (T->nb > 1) return ORC_ERR_INVALID_ARGUMENT; /* a tree with bands: orc_flux_bands */
     *out = NULL;
     orc_replay *r = calloc(1, sizeof(orc_replay));
     rec_buf_t rb;

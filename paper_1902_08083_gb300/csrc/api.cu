@@ -42,8 +42,10 @@ static WalkParams walk_params(const trevr_tree* t, const trevr_params* prm) {
   wp.variant = prm->walk_variant > 0 ? prm->walk_variant : kDefaultVariant;
   wp.bg_radius = prm->bg_radius;
   wp.tau_stop = prm->tau_stop > 0.0f ? prm->tau_stop : INFINITY;
-  // background sources and early termination are built into the merged-ray walk only
-  if (wp.bg_radius > 0.0f || prm->tau_stop > 0.0f) wp.variant = 3;
+  wp.sub_bucket = prm->sub_bucket;
+  // background sources, early termination and the sub-bucket trace are built into the
+  // merged-ray walk only
+  if (wp.bg_radius > 0.0f || prm->tau_stop > 0.0f || prm->sub_bucket) wp.variant = 3;
   return wp;
 }
 
@@ -57,6 +59,7 @@ static bool params_ok(const trevr_params* prm) {
   if (prm->walk_variant < 0 || prm->walk_variant > 3) return false;
   if (!(prm->bg_radius >= 0.0f) || !std::isfinite(prm->bg_radius)) return false;
   if (!(prm->tau_stop >= 0.0f)) return false;
+  if (prm->sub_bucket != 0 && prm->sub_bucket != 1) return false;
   return true;
 }
 
@@ -91,6 +94,15 @@ TreeView trevr_tree::view() const {
   v.src = src;
   v.src_order = src_order;
   v.n_nodes = d_n_nodes;
+  v.n_bands = n_bands;
+  v.bA = bA;
+  v.bLc = bLc;
+  v.bLs = bLs;
+  v.sp = sp;
+  v.aw = aw;
+  v.dbk = dbk;
+  v.nbr_first = nbr_first;
+  v.nbr = nbr;
   return v;
 }
 
@@ -116,11 +128,44 @@ int trevr_build_tree(const float* gas_xyz, const float* alpha, const float* weig
                          prm->bucket, (cudaStream_t)stream, out, &ms);
 }
 
-int trevr_compute_flux(const trevr_tree* t, const long long* sink_idx, long long n_sink,
-                       const trevr_params* prm, float* flux_out, int* sink_counters,
-                       trevr_stats* stats, void* stream) {
-  if (!t || !params_ok(prm)) return TREVR_ERR_INVALID_ARGUMENT;
-  if (n_sink < 0 || n_sink > (1ll << 30)) return TREVR_ERR_INVALID_ARGUMENT;
+int trevr_build_tree_bands(const float* gas_xyz, const float* alpha_bands, const float* weight,
+                           long long n_gas, const float* src_xyz, const float* lum_bands,
+                           long long n_src, int n_bands, const trevr_domain* dom,
+                           const trevr_params* prm, void* stream, trevr_tree** out) {
+  if (!out) return TREVR_ERR_INVALID_ARGUMENT;
+  *out = nullptr;
+  if (n_bands < 1 || n_bands > TREVR_MAX_BANDS) return TREVR_ERR_INVALID_ARGUMENT;
+  if (!gas_xyz || !alpha_bands || !dom || !prm) return TREVR_ERR_INVALID_ARGUMENT;
+  if (n_gas < 1 || n_gas > (1ll << 30) || n_src < 0 || n_src > (1ll << 30))
+    return TREVR_ERR_INVALID_ARGUMENT;
+  if ((long long)n_bands * n_gas > (1ll << 31) - 1 || (long long)n_bands * n_src > (1ll << 31) - 1)
+    return TREVR_ERR_INVALID_ARGUMENT;
+  if (n_src > 0 && (!src_xyz || !lum_bands)) return TREVR_ERR_INVALID_ARGUMENT;
+  if (prm->bucket < 1) return TREVR_ERR_INVALID_ARGUMENT;
+  if (!(dom->side > 0.0f) || !std::isfinite(dom->side)) return TREVR_ERR_INVALID_ARGUMENT;
+  for (int d = 0; d < 3; ++d)
+    if (!std::isfinite(dom->lo[d]) || !std::isfinite(dom->lo[d] + dom->side))
+      return TREVR_ERR_INVALID_ARGUMENT;
+  float ms = 0.0f;
+  return build_tree_bands_impl(gas_xyz, alpha_bands, weight, n_gas, src_xyz, lum_bands, n_src,
+                               n_bands, dom, prm->bucket, (cudaStream_t)stream, out, &ms);
+}
+
+int trevr_tree_set_smoothing(trevr_tree* t, const float* hsml, void* stream) {
+  if (!t || !hsml || t->n_bands > 1) return TREVR_ERR_INVALID_ARGUMENT;
+  return set_smoothing_impl(t, hsml, (cudaStream_t)stream);
+}
+
+int trevr_compute_flux_bands(const trevr_tree* t, const long long* sink_idx, long long n_sink,
+                             const trevr_params* prm, float* flux_out, int* sink_counters,
+                             trevr_stats* stats, void* stream) {
+  if (!t || !params_ok(prm) || t->n_bands < 1) return TREVR_ERR_INVALID_ARGUMENT;
+  if (prm->bg_radius > 0.0f || prm->tau_stop > 0.0f || prm->sub_bucket)
+    return TREVR_ERR_INVALID_ARGUMENT;
+  if (t->n_bands == 1)  // one band is the plain method on the same records
+    return trevr_compute_flux(t, sink_idx, n_sink, prm, flux_out, sink_counters, stats, stream);
+  if (n_sink < 0 || n_sink > (1ll << 30) || (long long)t->n_bands * n_sink > (1ll << 31) - 1)
+    return TREVR_ERR_INVALID_ARGUMENT;
   if (stats) std::memset(stats, 0, sizeof(*stats));
   if (n_sink == 0) return TREVR_OK;
   if (!flux_out) return TREVR_ERR_INVALID_ARGUMENT;
@@ -129,7 +174,63 @@ int trevr_compute_flux(const trevr_tree* t, const long long* sink_idx, long long
   WalkParams wp = walk_params(t, prm);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (stats) {
-    cudaMemsetAsync(t->d_stats, 0, 6 * sizeof(unsigned long long), s);
+    cudaMemsetAsync(t->d_stats, 0, 7 * sizeof(unsigned long long), s);
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+  }
+  cudaError_t err = launch_walk_bands(t->view(), sink_idx, (int)n_sink, wp, flux_out,
+                                      sink_counters, stats ? t->d_stats : nullptr, t->status, s);
+  if (err != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return cuda_to_error(err);
+  }
+  unsigned long long h[6] = {0, 0, 0, 0, 0, 0};
+  if (stats) {
+    cudaEventRecord(e1, s);
+    cudaMemcpyAsync(h, t->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s);
+  }
+  int status = 0;
+  cudaMemcpyAsync(&status, t->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  err = cudaStreamSynchronize(s);
+  float ms = 0.0f;
+  if (stats && err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (err != cudaSuccess) return cuda_to_error(err);
+  if (stats) {
+    stats->interactions = (long long)h[0];
+    stats->segments = (long long)h[1];
+    stats->src_nodes_visited = (long long)h[2];
+    stats->refine_expansions = (long long)h[3];
+    stats->cells_clipped = (long long)h[4];
+    stats->walk_ms = ms;
+  }
+  if (status) {
+    cudaMemsetAsync(t->status, 0, sizeof(int), s);
+    cudaStreamSynchronize(s);
+    return status_to_error(status);
+  }
+  return TREVR_OK;
+}
+
+int trevr_compute_flux(const trevr_tree* t, const long long* sink_idx, long long n_sink,
+                       const trevr_params* prm, float* flux_out, int* sink_counters,
+                       trevr_stats* stats, void* stream) {
+  if (!t || !params_ok(prm) || t->n_bands > 1) return TREVR_ERR_INVALID_ARGUMENT;
+  if (n_sink < 0 || n_sink > (1ll << 30)) return TREVR_ERR_INVALID_ARGUMENT;
+  if (prm->sub_bucket && (!t->nbr_first || prm->bg_radius > 0.0f || prm->tau_stop > 0.0f))
+    return TREVR_ERR_INVALID_ARGUMENT;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (n_sink == 0) return TREVR_OK;
+  if (!flux_out) return TREVR_ERR_INVALID_ARGUMENT;
+  if (!sink_idx && n_sink != t->n_gas) return TREVR_ERR_INVALID_ARGUMENT;
+  cudaStream_t s = (cudaStream_t)stream;
+  WalkParams wp = walk_params(t, prm);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (stats) {
+    cudaMemsetAsync(t->d_stats, 0, 7 * sizeof(unsigned long long), s);
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
@@ -143,7 +244,7 @@ int trevr_compute_flux(const trevr_tree* t, const long long* sink_idx, long long
   }
   if (!stats) return TREVR_OK;
   cudaEventRecord(e1, s);
-  unsigned long long h[6];
+  unsigned long long h[7];
   int status = 0;
   cudaMemcpyAsync(h, t->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(&status, t->status, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -159,6 +260,7 @@ int trevr_compute_flux(const trevr_tree* t, const long long* sink_idx, long long
   stats->refine_expansions = (long long)h[3];
   stats->cells_clipped = (long long)h[4];
   stats->rays_terminated = (long long)h[5];
+  stats->sub_bucket_segments = (long long)h[6];
   stats->walk_ms = ms;
   if (status) {
     cudaMemsetAsync(t->status, 0, sizeof(int), s);
@@ -171,9 +273,10 @@ int trevr_compute_flux(const trevr_tree* t, const long long* sink_idx, long long
 int trevr_compute_flux_moments(const trevr_tree* t, const long long* sink_idx, long long n_sink,
                                const trevr_params* prm, float* flux_out, float* fvec_out,
                                float* press_out, void* stream) {
-  if (!t || !params_ok(prm)) return TREVR_ERR_INVALID_ARGUMENT;
+  if (!t || !params_ok(prm) || t->n_bands > 1) return TREVR_ERR_INVALID_ARGUMENT;
   if (n_sink < 0 || n_sink > (1ll << 30)) return TREVR_ERR_INVALID_ARGUMENT;
-  if (prm->bg_radius > 0.0f || prm->tau_stop > 0.0f) return TREVR_ERR_INVALID_ARGUMENT;
+  if (prm->bg_radius > 0.0f || prm->tau_stop > 0.0f || prm->sub_bucket)
+    return TREVR_ERR_INVALID_ARGUMENT;
   if (n_sink == 0) return TREVR_OK;
   if (!flux_out || !fvec_out) return TREVR_ERR_INVALID_ARGUMENT;
   if (!sink_idx && n_sink != t->n_gas) return TREVR_ERR_INVALID_ARGUMENT;
@@ -197,10 +300,11 @@ int trevr_compute_flux_moments(const trevr_tree* t, const long long* sink_idx, l
 int trevr_compute_flux_backward(const trevr_tree* t, const long long* sink_idx, long long n_sink,
                                 const trevr_params* prm, const float* grad_flux, float* grad_lum,
                                 float* grad_alpha, void* stream) {
-  if (!t || !params_ok(prm)) return TREVR_ERR_INVALID_ARGUMENT;
+  if (!t || !params_ok(prm) || t->n_bands > 1) return TREVR_ERR_INVALID_ARGUMENT;
   if (n_sink < 0 || n_sink > (1ll << 30)) return TREVR_ERR_INVALID_ARGUMENT;
   if (n_sink > 0 && !grad_flux) return TREVR_ERR_INVALID_ARGUMENT;
-  if (prm->bg_radius > 0.0f || prm->tau_stop > 0.0f) return TREVR_ERR_INVALID_ARGUMENT;
+  if (prm->bg_radius > 0.0f || prm->tau_stop > 0.0f || prm->sub_bucket)
+    return TREVR_ERR_INVALID_ARGUMENT;
   if (n_sink > 0 && !sink_idx && n_sink != t->n_gas) return TREVR_ERR_INVALID_ARGUMENT;
   if ((t->n_src > 0 && !grad_lum) || !grad_alpha) return TREVR_ERR_INVALID_ARGUMENT;
   cudaStream_t s = (cudaStream_t)stream;
@@ -243,7 +347,7 @@ int trevr_batch_create(trevr_tree* const* trees, int n_trees, trevr_batch** out)
   *out = nullptr;
   if (!trees || n_trees < 1) return TREVR_ERR_INVALID_ARGUMENT;
   for (int b = 0; b < n_trees; ++b)
-    if (!trees[b]) return TREVR_ERR_INVALID_ARGUMENT;
+    if (!trees[b] || trees[b]->n_bands > 1) return TREVR_ERR_INVALID_ARGUMENT;
   trevr_batch* B = new trevr_batch();
   std::memset(B, 0, sizeof(*B));
   cudaGetDevice(&B->device);
@@ -297,7 +401,8 @@ static int batch_items(trevr_batch* B, int item) {
 int trevr_compute_flux_batched(trevr_batch* B, const trevr_params* prm, float* const* flux_out,
                                trevr_stats* stats, void* stream) {
   if (!B || !flux_out || !params_ok(prm)) return TREVR_ERR_INVALID_ARGUMENT;
-  if (prm->bg_radius > 0.0f || prm->tau_stop > 0.0f) return TREVR_ERR_INVALID_ARGUMENT;
+  if (prm->bg_radius > 0.0f || prm->tau_stop > 0.0f || prm->sub_bucket)
+    return TREVR_ERR_INVALID_ARGUMENT;
   const int item = prm->sinks_per_warp > 0 ? prm->sinks_per_warp : 64;
   if (item % 32 != 0 || item > (1 << 20)) return TREVR_ERR_INVALID_ARGUMENT;
   int rc = batch_items(B, item);
@@ -315,6 +420,7 @@ int trevr_compute_flux_batched(trevr_batch* B, const trevr_params* prm, float* c
   wp.variant = prm->walk_variant > 0 ? prm->walk_variant : kDefaultVariant;
   wp.bg_radius = 0.0f;
   wp.tau_stop = INFINITY;
+  wp.sub_bucket = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
@@ -482,7 +588,8 @@ void trevr_tree_free(trevr_tree* t) {
   void* ptrs[] = {t->key, t->perm,   t->rank,   t->leaf_of, t->pos,    t->w,      t->nA,
                   t->nB,  t->nS,     t->nT,     t->nl2,     t->ndepth, t->nfirst, t->ncount,
                   t->nglo, t->nghi,  t->src,    t->src_order, t->levels, t->d_n_nodes,
-                  t->status, t->d_stats, t->src_leaf, t->nW};
+                  t->status, t->d_stats, t->src_leaf, t->nW, t->bA, t->bLc, t->bLs, t->sp, t->aw,
+                  t->dbk, t->nbr_first, t->nbr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   cudaSetDevice(cur);

@@ -101,6 +101,10 @@ static void exclusive_scan(unsigned* data, int n, unsigned* scratch, cudaStream_
   }
 }
 
+void exclusive_scan_u32(unsigned* data, int n, unsigned* scratch, cudaStream_t s) {
+  exclusive_scan(data, n, scratch, s);
+}
+
 // ------------------------------------------------------------------------------------
 // Stable LSD radix sort, 8-bit digits. counts layout: [digit][tile].
 // ------------------------------------------------------------------------------------

@@ -53,6 +53,17 @@ struct TreeView {
   const float4* src;  // (y.x, y.y, y.z, L)
   const int* src_order;
   const int* n_nodes;  // device scalar
+  // several bands (trevr_build_tree_bands): up to 4 per record, unused slots 0
+  int n_bands;         // 0 for a single-band tree
+  const float4* bA;    // per cell: mean absorption of each band
+  const float4* bLc;   // per cell: luminosity of each band
+  const float4* bLs;   // per sorted source: luminosity of each band
+  // sub-bucket particle trace (null unless smoothing lengths are set)
+  const float4* sp;    // per sorted particle (x, y, z, h)
+  const float* aw;     // per sorted particle alpha * w
+  const float* dbk;    // per cell: alpha spread of a leaf's particles
+  const unsigned* nbr_first;
+  const int* nbr;
 };
 
 }  // namespace trevr
@@ -102,6 +113,17 @@ struct trevr_tree {
   int* src_order;
   int* src_leaf;  // leaf cell of each sorted source
   double* nW;     // sum of the volume weights of each cell (for the adjoint)
+  int n_bands;    // several bands (trevr_build_tree_bands), else 0
+  float4* bA;     // per cell, band means of the absorption
+  float4* bLc;    // per cell, band luminosities
+  float4* bLs;    // per sorted source, band luminosities
+  // sub-bucket particle trace (trevr_tree_set_smoothing), else null
+  float4* sp;        // per sorted particle (x, y, z, h)
+  float* aw;         // per sorted particle alpha * w (absorbing mass kappa m)
+  float* dbk;        // per cell: max - min of alpha over a leaf's particles (0 inside)
+  unsigned* nbr_first;  // per cell + 1: start of the leaf's neighbour list
+  int* nbr;          // sorted particle indices whose kernel support meets the leaf
+  long long n_nbr;
   int h_levels[2 * trevr::kMaxLevels];  // host copy of the level ranges
   // bookkeeping
   int* levels;    // kMaxLevels x 2 (begin, end)
@@ -118,6 +140,11 @@ int build_tree_impl(const float* gas_xyz, const float* alpha, const float* weigh
                     const float* src_xyz, const float* src_lum, long long n_src,
                     const trevr_domain* dom, int bucket, cudaStream_t s, trevr_tree** out,
                     float* build_ms);
+// ---- bands.cu
+int build_tree_bands_impl(const float* gas_xyz, const float* alpha_bands, const float* weight,
+                          long long n_gas, const float* src_xyz, const float* lum_bands,
+                          long long n_src, int n_bands, const trevr_domain* dom, int bucket,
+                          cudaStream_t s, trevr_tree** out, float* build_ms);
 
 // ---- build.cu: stable LSD radix sort of (uint64 key, uint32 value) pairs
 struct SortScratch {
@@ -132,6 +159,10 @@ int scan_tiles(int n);
 // sorts (k, v) in place by bits [0, bits) of k
 void radix_sort(unsigned long long* k, unsigned* v, int n, int bits, const SortScratch& S,
                 cudaStream_t s);
+// exclusive prefix sum of n words in place; scratch holds scan_scratch_words(n) words
+void exclusive_scan_u32(unsigned* data, int n, unsigned* scratch, cudaStream_t s);
+// ---- subbucket.cu
+int set_smoothing_impl(trevr_tree* t, const float* h, cudaStream_t s);
 
 // ---- walk.cu
 struct WalkParams {
@@ -143,6 +174,7 @@ struct WalkParams {
   int variant;         // 1 = per-lane walk, 2 = warp-shared walk
   float bg_radius;     // > 0: sources are background sources on this sphere (Sec. 2.2.4)
   float tau_stop;      // early ray termination threshold (+inf = off)
+  int sub_bucket;      // sub-bucket particle trace (the tree has smoothing lengths)
 };
 // accumulators of the adjoint (FP64, zeroed by the caller)
 struct AdjointArgs {
@@ -166,6 +198,9 @@ cudaError_t launch_walk(const TreeView& T, const long long* sink_idx, int n_sink
                         const WalkParams& wp, float* flux_out, int* counters,
                         unsigned long long* stats, int* status, int block_size,
                         cudaStream_t s);
+cudaError_t launch_walk_bands(const TreeView& T, const long long* sink_idx, int n_sink,
+                              const WalkParams& wp, float* flux_out, int* counters,
+                              unsigned long long* stats, int* status, cudaStream_t s);
 
 // ---- adjoint.cu: from the cell accumulators to the caller's gradients
 cudaError_t adjoint_finalize(const trevr_tree* t, const AdjointArgs& J, float* grad_lum,

@@ -97,16 +97,17 @@ __device__ __forceinline__ void slab_g(int k, float lo, float hi, float p, float
 }  // namespace
 
 struct SinkCounters {
-  int rays = 0, segs = 0, visit = 0, ref = 0, clip = 0, cut = 0;
+  int rays = 0, segs = 0, visit = 0, ref = 0, clip = 0, cut = 0, sub = 0;
 };
 
 // warp-reduce the counters and add them to the device totals (all lanes call it)
 __device__ __forceinline__ void add_stats(const SinkCounters& c, unsigned long long* stats) {
-  unsigned long long v[6] = {(unsigned long long)c.rays, (unsigned long long)c.segs,
+  unsigned long long v[7] = {(unsigned long long)c.rays, (unsigned long long)c.segs,
                              (unsigned long long)c.visit, (unsigned long long)c.ref,
-                             (unsigned long long)c.clip, (unsigned long long)c.cut};
+                             (unsigned long long)c.clip, (unsigned long long)c.cut,
+                             (unsigned long long)c.sub};
 #pragma unroll
-  for (int q = 0; q < 6; ++q) {
+  for (int q = 0; q < 7; ++q) {
     unsigned long long x = v[q];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
@@ -568,11 +569,85 @@ __device__ __forceinline__ void warp_atomic_add(double* base, int key, float v) 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Sub-bucket particle trace (Sec. 2.2.3, 3.1.3). The absorption below the bucket
+// scale is the SPH field sum_j alpha_j w_j W(|x - x_j|, h_j), W the cubic spline
+// of support 2h. Along a ray at impact parameter b from x_j, with s measured from
+// the closest approach, W depends on r = sqrt(b^2 + s^2). Its integral over s is
+// taken by 6-point Gauss-Legendre quadrature (nodes and weights of Abramowitz &
+// Stegun, Table 25.4) on each piece between the break points s = 0, r = h and
+// r = 2h, where the integrand is smooth.
+__device__ __forceinline__ float spline_w(float b2, float u, float invh) {
+  const float q = __fmul_rn(__fsqrt_rn(__fadd_rn(b2, __fmul_rn(u, u))), invh);
+  if (q < 1.0f) return 1.0f - 1.5f * q * q + 0.75f * q * q * q;
+  if (q < 2.0f) {
+    const float t = 2.0f - q;
+    return 0.25f * t * t * t;
+  }
+  return 0.0f;
+}
+
+// Gauss-Legendre rule on [a, c] (6 points)
+__device__ __forceinline__ float gl6(float b2, float a, float c, float invh) {
+  if (!(c > a)) return 0.0f;
+  const float x[3] = {0.2386191860831969f, 0.6612093864662645f, 0.9324695142031521f};
+  const float w[3] = {0.4679139345726910f, 0.3607615730481386f, 0.1713244923791704f};
+  const float m = 0.5f * (a + c), hw = 0.5f * (c - a);
+  float acc = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    acc += w[k] * (spline_w(b2, m - hw * x[k], invh) + spline_w(b2, m + hw * x[k], invh));
+  return acc * hw;
+}
+
+// integral of W over u in [0, s] (s >= 0), W normalised by 1/(pi h^3)
+__device__ __forceinline__ float kernel_half(float b2, float s, float H, float invh) {
+  const float h2 = H * H;
+  const float u1 = b2 < h2 ? sqrtf(h2 - b2) : 0.0f;
+  const float u2 = b2 < 4.0f * h2 ? sqrtf(4.0f * h2 - b2) : 0.0f;
+  const float a1 = fminf(s, u1), a2 = fminf(s, u2);
+  return (gl6(b2, 0.0f, a1, invh) + gl6(b2, a1, a2, invh)) * (invh * invh * invh * 0.318309886f);
+}
+
+__device__ __forceinline__ float kernel_line(float b2, float s0, float s1, float H) {
+  const float invh = 1.0f / H;
+  const float g1 = s1 >= 0.0f ? kernel_half(b2, s1, H, invh) : -kernel_half(b2, -s1, H, invh);
+  const float g0 = s0 >= 0.0f ? kernel_half(b2, s0, H, invh) : -kernel_half(b2, -s0, H, invh);
+  return g1 - g0;
+}
+
+// optical depth of the chord p + t d, t in [t0, t1], through the particles listed for
+// leaf `box`, the receiving particle (sorted index si) left out
+__device__ float sub_bucket_tau(const TreeView& T, int box, int si, float px, float py, float pz,
+                                float dx, float dy, float dz, float s2, float len, float t0,
+                                float t1) {
+  CSum acc;
+  const unsigned k1 = __ldg(&T.nbr_first[box + 1]);
+  for (unsigned k = __ldg(&T.nbr_first[box]); k < k1; ++k) {
+    const int j = __ldg(&T.nbr[k]);
+    if (j == si) continue;
+    const float a = __ldg(&T.aw[j]);
+    if (!(a > 0.0f)) continue;
+    const float4 q = __ldg(&T.sp[j]);
+    const float ux = q.x - px, uy = q.y - py, uz = q.z - pz;
+    const float tc = (ux * dx + uy * dy + uz * dz) / s2;
+    const float ex = ux - tc * dx, ey = uy - tc * dy, ez = uz - tc * dz;
+    const float b2 = ex * ex + ey * ey + ez * ez;
+    if (b2 >= 4.0f * q.w * q.w) continue;
+    acc.add(a * kernel_line(b2, (t0 - tc) * len, (t1 - tc) * len, q.w));
+  }
+  return acc.get();
+}
+
 // Rays from the sinks of the lanes in `on` to (q, L) inside cell C; every lane
 // of the warp must call it (the loop runs while any lane has cells left).
 // STOP: early ray termination (Sec. 5): a lane whose running optical depth passes
 // P.tau_stop drops the rest of its ray, and the ray adds nothing.
-template <bool ADJ, bool MOM, bool STOP = false>
+// NB > 1: several bands (2 or 4 slots of the band records): every band sums its own
+// optical depth over the shared segments, and F[b] gets band b's flux.
+// SUB: the sub-bucket particle trace for leaves whose own particles ask for
+// refinement (the sink's sorted index si is left out of the sum).
+template <bool ADJ, bool MOM, bool STOP = false, int NB = 1, bool SUB = false>
 __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P, const bool on,
                                          const float px, const float py, const float pz,
                                          const int S, const int dS, const int* anc, int* rst,
@@ -581,7 +656,11 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
                                          const float qy, const float qz, const float L,
                                          const int src_j, const float gk, const int stack_limit,
                                          const int box_limit, int* status, const AdjointArgs& J,
-                                         SinkCounters& cnt, CSum& F, Moments* mom) {
+                                         SinkCounters& cnt, CSum* F, Moments* mom,
+                                         const int si = -1) {
+  static_assert(NB == 1 || NB == 2 || NB == 4, "band slots: 1, 2 or 4");
+  static_assert(!SUB || (!ADJ && !MOM && NB == 1), "sub-bucket trace: plain flux only");
+  static_assert(NB == 1 || !(ADJ || MOM || STOP), "bands: plain flux only");
   const unsigned FULL = 0xffffffffu;
   float dx = 0.0f, dy = 0.0f, dz = 0.0f, s2 = 1.0f, len = 1.0f, ix = 0.0f, iy = 0.0f, iz = 0.0f;
   int nCs = 0, nSs = 0, nb = 0, dstar = 0;
@@ -611,6 +690,7 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
   }
   const bool traced = active;
   CSum tau;
+  CSum taub[NB];  // (NB > 1) optical depth of each band
   bool cut = false;
   int b = 0, rsp = 0, boxes = 0, pass = 1;
   // adjoint: the first pass records its segment cells and lengths (up to kSegBuf),
@@ -641,7 +721,18 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
           ++cnt.rays;
           active = false;
         } else if (!ADJ) {
-          F.add(f);
+          if (NB > 1) {
+            // the band luminosities of the source, or of the merged cell C
+            const float4 Lb = src_j >= 0 ? __ldg(&T.bLs[src_j]) : __ldg(&T.bLc[C]);
+            F[0].add(Lb.x * expf(-taub[0].get()) / (kFourPi * s2));
+            F[1].add(Lb.y * expf(-taub[1].get()) / (kFourPi * s2));
+            if (NB > 2) {
+              F[NB > 2 ? 2 : 0].add(Lb.z * expf(-taub[NB > 2 ? 2 : 0].get()) / (kFourPi * s2));
+              F[NB > 2 ? 3 : 0].add(Lb.w * expf(-taub[NB > 2 ? 3 : 0].get()) / (kFourPi * s2));
+            }
+          } else {
+            F[0].add(f);
+          }
           if (MOM) {
             const float il = 1.0f / len;
             const float n0 = -dx * il, n1 = -dy * il, n2 = -dz * il;
@@ -731,7 +822,22 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
                 akey = box;
                 aval = -gk * fcur * l;
               } else {
-                tau.add(a.w * l);
+                if (NB > 1) {
+                  const float4 ab = __ldg(&T.bA[box]);
+                  taub[0].add(ab.x * l);
+                  taub[1].add(ab.y * l);
+                  if (NB > 2) {
+                    taub[NB > 2 ? 2 : 0].add(ab.z * l);
+                    taub[NB > 2 ? 3 : 0].add(ab.w * l);
+                  }
+                } else if (SUB && (P.tau_ref <= 0.0f ||
+                                   __fmul_rn(__ldg(&T.dbk[box]), l) > P.tau_ref)) {
+                  // a bucket that still asks for refinement: trace its particles
+                  tau.add(sub_bucket_tau(T, box, si, px, py, pz, dx, dy, dz, s2, len, t0, t1));
+                  ++cnt.sub;
+                } else {
+                  tau.add(a.w * l);
+                }
                 if (!ADJ && STOP && tau.get() > P.tau_stop) {
                   cut = true;  // the rest of the ray is not traced
                   b = nb;
@@ -791,11 +897,12 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
 // o before its ray is traced, in fp32 as d = c - o, s = sqrt((dx^2 + dy^2) + dz^2),
 // q = o + d * (R / s); the ray then ends in the leaf that holds q, whose ancestors the
 // lane finds by descending the cut planes from the root and keeps for that ray.
-template <bool ADJ, bool MERGE, bool MOM = false, bool BG = false, bool STOP = false>
+template <bool ADJ, bool MERGE, bool MOM = false, bool BG = false, bool STOP = false, int NB = 1,
+          bool SUB = false>
 __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P, const bool has,
                                           const int i, const float gk, WarpStack& ws,
                                           int* status, const AdjointArgs& J,
-                                          SinkCounters& cnt, CSum& F, Moments* mom = nullptr) {
+                                          SinkCounters& cnt, CSum* F, Moments* mom = nullptr) {
   const unsigned FULL = 0xffffffffu;
   const unsigned lane = threadIdx.x & 31u;
   const int stack_limit = P.stack_depth < kDepth ? P.stack_depth : kDepth;
@@ -843,12 +950,13 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
         for (int d = 0; d <= mn && cpath[d] == anc[d]; ++d) onp |= 1ull << d;
         pp = cpath;
       }
-      warp_ray<ADJ, MOM, STOP>(T, P, pnd, px, py, pz, S, dS, anc, rst, onp, pp, pC, pdC, pqx, pqy,
-                         pqz, pL, psrc, gk, stack_limit, box_limit, status, J, cnt, F, mom);
+      warp_ray<ADJ, MOM, STOP, NB, SUB>(T, P, pnd, px, py, pz, S, dS, anc, rst, onp, pp, pC, pdC, pqx, pqy,
+                         pqz, pL, psrc, gk, stack_limit, box_limit, status, J, cnt, F, mom,
+                         i);
     } else {
-      warp_ray<ADJ, MOM, STOP>(T, P, pnd, px, py, pz, S, dS, anc, rst, on_path, ws.path, pC, pdC,
+      warp_ray<ADJ, MOM, STOP, NB, SUB>(T, P, pnd, px, py, pz, S, dS, anc, rst, on_path, ws.path, pC, pdC,
                          pqx, pqy, pqz, pL, psrc, gk, stack_limit, box_limit, status, J, cnt, F,
-                         mom);
+                         mom, i);
     }
     pnd = false;
     pbg = false;
@@ -935,8 +1043,9 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
         }
       }
     } else if (accM) {
-      warp_ray<ADJ, MOM, STOP>(T, P, acc, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX, s.x,
-                         s.y, s.z, s.w, -1, gk, stack_limit, box_limit, status, J, cnt, F, mom);
+      warp_ray<ADJ, MOM, STOP, NB, SUB>(T, P, acc, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX, s.x,
+                         s.y, s.z, s.w, -1, gk, stack_limit, box_limit, status, J, cnt, F, mom,
+                         i);
     }
     if (opnM) {
       const int4 t = __ldg(&T.nT[X]);
@@ -957,9 +1066,9 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
               psrc = jj;
             }
           } else {
-            warp_ray<ADJ, MOM, STOP>(T, P, opn, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX,
+            warp_ray<ADJ, MOM, STOP, NB, SUB>(T, P, opn, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX,
                                y.x, y.y, y.z, y.w, jj, gk, stack_limit, box_limit, status, J, cnt,
-                               F, mom);
+                               F, mom, i);
           }
         }
       } else {
@@ -985,8 +1094,9 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
 
 // 8 blocks of 128 per SM (at most 64 registers): measured 4% faster forward and 8%
 // faster adjoint than the compiler's own 70 registers at 7 blocks
-template <bool ADJ, bool MERGE, bool MOM = false, bool BG = false, bool STOP = false>
-__global__ void __launch_bounds__(128, 8) walk_warp_kernel(TreeView T, const long long* sink_idx,
+template <bool ADJ, bool MERGE, bool MOM = false, bool BG = false, bool STOP = false, int NB = 1,
+          bool SUB = false>
+__global__ void __launch_bounds__(128, (NB > 1 || SUB) ? 4 : 8) walk_warp_kernel(TreeView T, const long long* sink_idx,
                                                         int n_sink, WalkParams P, SinkOut out,
                                                         unsigned long long* stats, int* status,
                                                         AdjointArgs J) {
@@ -1001,15 +1111,16 @@ __global__ void __launch_bounds__(128, 8) walk_warp_kernel(TreeView T, const lon
     PlainMap<ADJ> map{&T, sink_idx, J.grad_flux, status};
     has = map(k, i, slot, g);
     if (!has && !ADJ && sink_idx) {
-      if (out.flux) out.flux[k] = 0.0f;
+      if (out.flux)
+        for (int b = 0; b < (NB > 1 ? T.n_bands : 1); ++b) out.flux[(size_t)b * out.n_out + k] = 0.0f;
       if (out.counters) reinterpret_cast<int4*>(out.counters)[k] = make_int4(0, 0, 0, 0);
     }
   }
-  CSum F;
+  CSum F[NB];
   Moments mom;
   if (__any_sync(0xffffffffu, has))
-    warp_walk<ADJ, MERGE, MOM, BG, STOP>(T, P, has, i, g, ws, status, J, cnt, F,
-                                         MOM ? &mom : nullptr);
+    warp_walk<ADJ, MERGE, MOM, BG, STOP, NB, SUB>(T, P, has, i, g, ws, status, J, cnt, F,
+                                                  MOM ? &mom : nullptr);
   if (MOM && has) {
 #pragma unroll
     for (int q = 0; q < 3; ++q)
@@ -1019,7 +1130,14 @@ __global__ void __launch_bounds__(128, 8) walk_warp_kernel(TreeView T, const lon
       if (out.press) out.press[(size_t)q * out.n_out + slot] = mom.v[3 + q].get();
   }
   if (!ADJ && has) {
-    if (out.flux) out.flux[slot] = F.get();
+    if (NB > 1) {
+      // band-major output: band b of sink slot at b * n_out + slot
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+        if (out.flux && b < T.n_bands) out.flux[(size_t)b * out.n_out + slot] = F[b].get();
+    } else if (out.flux) {
+      out.flux[slot] = F[0].get();
+    }
     if (out.counters)
       reinterpret_cast<int4*>(out.counters)[slot] = make_int4(cnt.rays, cnt.segs, cnt.visit, cnt.ref);
   }
@@ -1053,7 +1171,7 @@ __global__ void __launch_bounds__(BS, 1024 / BS) walk_warp_batched_kernel(
       const bool has = i < end;
       SinkCounters cnt;
       CSum F;
-      warp_walk<false, MERGE>(T, Pt, has, i, 0.0f, ws, status, AdjointArgs{}, cnt, F);
+      warp_walk<false, MERGE>(T, Pt, has, i, 0.0f, ws, status, AdjointArgs{}, cnt, &F);
       if (has) flux_out[w.x][T.perm[i]] = F.get();
       tot.rays += cnt.rays;
       tot.segs += cnt.segs;
@@ -1122,6 +1240,24 @@ cudaError_t launch_walk_moments(const TreeView& T, const long long* sink_idx, in
   return cudaGetLastError();
 }
 
+// Several bands: 2 band slots for 2 bands, 4 slots for 3 or 4 (an unused slot holds
+// zeros and is not written). One band is the plain walk.
+cudaError_t launch_walk_bands(const TreeView& T, const long long* sink_idx, int n_sink,
+                              const WalkParams& wp, float* flux_out, int* counters,
+                              unsigned long long* stats, int* status, cudaStream_t s) {
+  if (n_sink <= 0) return cudaSuccess;
+  const dim3 grid((n_sink + 127) / 128);
+  const SinkOut o{flux_out, counters, nullptr, nullptr, n_sink};
+  if (T.n_bands <= 2)
+    walk_warp_kernel<false, true, false, false, false, 2><<<grid, 128, 0, s>>>(
+        T, sink_idx, n_sink, wp, o, stats, status, AdjointArgs{});
+  else
+    walk_warp_kernel<false, true, false, false, false, 4><<<grid, 128, 0, s>>>(
+        T, sink_idx, n_sink, wp, o, stats, status, AdjointArgs{});
+  note_launch();
+  return cudaGetLastError();
+}
+
 static int chunk_of(const WalkParams& wp) {
   return wp.sinks_per_warp > 0 ? wp.sinks_per_warp : kDefaultChunk;
 }
@@ -1132,6 +1268,13 @@ cudaError_t launch_walk(const TreeView& T, const long long* sink_idx, int n_sink
                         cudaStream_t s) {
   if (n_sink <= 0) return cudaSuccess;
   (void)block_size;
+  if (wp.sub_bucket) {
+    walk_warp_kernel<false, true, false, false, false, 1, true><<<(n_sink + 127) / 128, 128, 0, s>>>(
+        T, sink_idx, n_sink, wp, SinkOut{flux_out, counters, nullptr, nullptr, n_sink}, stats,
+        status, AdjointArgs{});
+    note_launch();
+    return cudaGetLastError();
+  }
   if (wp.bg_radius > 0.0f || wp.tau_stop < INFINITY) {
     const dim3 grid((n_sink + 127) / 128);
     const SinkOut o{flux_out, counters, nullptr, nullptr, n_sink};

@@ -33,7 +33,8 @@ EXPORTS = (
     "trevr_tree_info",
     "trevr_tree_export", "trevr_tree_free", "trevr_status_string", "trevr_kernel_launches",
     "trevr_morton_sort_noalloc", "trevr_batch_create", "trevr_compute_flux_batched",
-    "trevr_batch_check", "trevr_batch_free",
+    "trevr_batch_check", "trevr_batch_free", "trevr_build_tree_bands", "trevr_compute_flux_bands",
+    "trevr_tree_set_smoothing",
 )
 NOALLOC_MAX_N = 1 << 20
 
@@ -54,7 +55,7 @@ class Params(ctypes.Structure):
                 ("bucket", ctypes.c_int), ("sinks_per_warp", ctypes.c_int),
                 ("block_size", ctypes.c_int), ("stack_depth", ctypes.c_int),
                 ("walk_variant", ctypes.c_int), ("bg_radius", ctypes.c_float),
-                ("tau_stop", ctypes.c_float)]
+                ("tau_stop", ctypes.c_float), ("sub_bucket", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -62,7 +63,8 @@ class Stats(ctypes.Structure):
                 ("src_nodes_visited", ctypes.c_longlong),
                 ("refine_expansions", ctypes.c_longlong), ("cells_clipped", ctypes.c_longlong),
                 ("build_ms", ctypes.c_float),
-                ("walk_ms", ctypes.c_float), ("rays_terminated", ctypes.c_longlong)]
+                ("walk_ms", ctypes.c_float), ("rays_terminated", ctypes.c_longlong),
+                ("sub_bucket_segments", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -89,6 +91,15 @@ def load_library(path: str = LIB_PATH):
         lib.trevr_compute_flux.argtypes = [P, P, ll, ctypes.POINTER(Params), P, P,
                                            ctypes.POINTER(Stats), P]
         lib.trevr_compute_flux.restype = ctypes.c_int
+        lib.trevr_build_tree_bands.argtypes = [P, P, P, ll, P, P, ll, ctypes.c_int,
+                                               ctypes.POINTER(Domain), ctypes.POINTER(Params), P,
+                                               ctypes.POINTER(P)]
+        lib.trevr_build_tree_bands.restype = ctypes.c_int
+        lib.trevr_compute_flux_bands.argtypes = [P, P, ll, ctypes.POINTER(Params), P, P,
+                                                 ctypes.POINTER(Stats), P]
+        lib.trevr_compute_flux_bands.restype = ctypes.c_int
+        lib.trevr_tree_set_smoothing.argtypes = [P, P, P]
+        lib.trevr_tree_set_smoothing.restype = ctypes.c_int
         lib.trevr_compute_flux_backward.argtypes = [P, P, ll, ctypes.POINTER(Params), P, P, P,
                                                     P]
         lib.trevr_compute_flux_backward.restype = ctypes.c_int
@@ -140,14 +151,17 @@ def _stream_ptr(stream=None):
 
 
 def make_params(theta=0.75, tau_ref=0.1, bucket=8, sinks_per_warp=0, block_size=0,
-                stack_depth=0, walk_variant=0, bg_radius=0.0, tau_stop=0.0):
+                stack_depth=0, walk_variant=0, bg_radius=0.0, tau_stop=0.0, sub_bucket=0):
     return Params(float(theta), float(tau_ref), int(bucket), int(sinks_per_warp),
                   int(block_size), int(stack_depth), int(walk_variant), float(bg_radius),
-                  float(tau_stop))
+                  float(tau_stop), int(sub_bucket))
 
 
 class Tree:
-    """A radiation tree built on the GPU (trevr_build_tree); owns the C handle."""
+    """A radiation tree built on the GPU (trevr_build_tree); owns the C handle.
+
+    alpha (N,) and src_lum (S,); or, for several bands (trevr_build_tree_bands),
+    alpha (B, N) and src_lum (B, S)."""
 
     def __init__(self, gas_xyz, alpha, src_xyz, src_lum, weight=None, lo=(0.0, 0.0, 0.0),
                  side=1.0, bucket=8, stream=None):
@@ -166,14 +180,32 @@ class Tree:
         dom = Domain((ctypes.c_float * 3)(*[float(v) for v in lo]), float(side))
         prm = make_params(bucket=bucket)
         h = ctypes.c_void_p()
-        rc = lib.trevr_build_tree(
-            _dev_ptr(gas_xyz, torch.float32, "gas_xyz"), _dev_ptr(alpha, torch.float32, "alpha"),
-            _dev_ptr(weight, torch.float32, "weight"), self.n_gas,
-            _dev_ptr(src_xyz, torch.float32, "src_xyz") if self.n_src else None,
-            _dev_ptr(src_lum, torch.float32, "src_lum") if self.n_src else None, self.n_src,
-            ctypes.byref(dom), ctypes.byref(prm), _stream_ptr(stream), ctypes.byref(h))
+        self.n_bands = 0
+        if alpha.dim() == 2:
+            self.n_bands = int(alpha.shape[0])
+            if alpha.shape[1] != self.n_gas or (self.n_src and
+                                                tuple(src_lum.shape) != (self.n_bands, self.n_src)):
+                raise ValueError("alpha (B, N) and src_lum (B, S) must have the same B")
+            rc = lib.trevr_build_tree_bands(
+                _dev_ptr(gas_xyz, torch.float32, "gas_xyz"),
+                _dev_ptr(alpha.contiguous(), torch.float32, "alpha"),
+                _dev_ptr(weight, torch.float32, "weight"), self.n_gas,
+                _dev_ptr(src_xyz, torch.float32, "src_xyz") if self.n_src else None,
+                _dev_ptr(src_lum.contiguous(), torch.float32, "src_lum") if self.n_src else None,
+                self.n_src, self.n_bands, ctypes.byref(dom), ctypes.byref(prm),
+                _stream_ptr(stream), ctypes.byref(h))
+            where = "trevr_build_tree_bands"
+        else:
+            rc = lib.trevr_build_tree(
+                _dev_ptr(gas_xyz, torch.float32, "gas_xyz"),
+                _dev_ptr(alpha, torch.float32, "alpha"),
+                _dev_ptr(weight, torch.float32, "weight"), self.n_gas,
+                _dev_ptr(src_xyz, torch.float32, "src_xyz") if self.n_src else None,
+                _dev_ptr(src_lum, torch.float32, "src_lum") if self.n_src else None, self.n_src,
+                ctypes.byref(dom), ctypes.byref(prm), _stream_ptr(stream), ctypes.byref(h))
+            where = "trevr_build_tree"
         if rc != TREVR_OK:
-            raise TrevrError(rc, "trevr_build_tree")
+            raise TrevrError(rc, where)
         self._h = h
         self.bucket = bucket
         self.side = float(side)
@@ -197,6 +229,17 @@ class Tree:
             self.free()
         except Exception:
             pass
+
+    def set_smoothing(self, hsml, stream=None):
+        """Smoothing lengths (N,) fp32 on the device, caller order, for the sub-bucket
+        particle trace (trevr_tree_set_smoothing); then pass sub_bucket=1."""
+        hsml = hsml.contiguous()
+        if hsml.numel() != self.n_gas:
+            raise ValueError(f"hsml has {hsml.numel()} elements, expected {self.n_gas}")
+        rc = self._lib.trevr_tree_set_smoothing(self._h, _dev_ptr(hsml, torch.float32, "hsml"),
+                                                _stream_ptr(stream))
+        if rc != TREVR_OK:
+            raise TrevrError(rc, "trevr_tree_set_smoothing")
 
     def export(self, stream=None):
         """Copy the tree into torch tensors on the tree's device (see trevr_tree_export)."""
@@ -250,6 +293,35 @@ def compute_flux(tree: Tree, theta=0.75, tau_ref=0.1, sink_idx=None, out=None, c
                                 ctypes.byref(st) if st is not None else None, _stream_ptr(stream))
     if rc != TREVR_OK:
         raise TrevrError(rc, "trevr_compute_flux")
+    res = [out]
+    if counters:
+        res.append(cnt)
+    if stats:
+        res.append(st.as_dict())
+    return res[0] if len(res) == 1 else tuple(res)
+
+
+def compute_flux_bands(tree: Tree, theta=0.75, tau_ref=0.1, sink_idx=None, out=None,
+                       counters=False, stats=False, stream=None, **tuning):
+    """Flux of every band (trevr_compute_flux_bands) for a tree built with alpha (B, N):
+    returns (B, n) fp32, plus counters / stats as compute_flux."""
+    lib = tree._lib
+    n = tree.n_gas if sink_idx is None else int(sink_idx.shape[0])
+    nb = max(tree.n_bands, 1)
+    if out is None:
+        out = torch.empty(nb, n, dtype=torch.float32, device=tree.device)
+    elif tuple(out.shape) != (nb, n):
+        raise ValueError(f"out has shape {tuple(out.shape)}, expected {(nb, n)}")
+    cnt = torch.empty(n, 4, dtype=torch.int32, device=tree.device) if counters else None
+    st = Stats() if stats else None
+    prm = make_params(theta, tau_ref, tree.bucket, **tuning)
+    rc = lib.trevr_compute_flux_bands(tree.handle, _dev_ptr(sink_idx, torch.int64, "sink_idx"),
+                                      n, ctypes.byref(prm), _dev_ptr(out, torch.float32, "out"),
+                                      _dev_ptr(cnt, torch.int32, "counters"),
+                                      ctypes.byref(st) if st is not None else None,
+                                      _stream_ptr(stream))
+    if rc != TREVR_OK:
+        raise TrevrError(rc, "trevr_compute_flux_bands")
     res = [out]
     if counters:
         res.append(cnt)

@@ -174,6 +174,31 @@ def background_shell(n_gas=1 << 14, n_bg=20000, radius=0.45, l_total=1.0, seed=9
                     seed=seed, radius=radius, l_total=l_total)
 
 
+def knn_smoothing(xyz, k=32):
+    """SPH-style smoothing lengths: h_j = half the distance from particle j to its k-th
+    nearest neighbour, so that the kernel support 2h holds about k particles."""
+    from scipy.spatial import cKDTree
+    pts = np.asarray(xyz, np.float64).T
+    d, _ = cKDTree(pts).query(pts, k=k + 1)
+    return (0.5 * d[:, -1]).astype(np.float32)
+
+
+def sub_bucket_problem(n_gas=1 << 12, n_src=32, seed=11, alpha0=2.0, sigma=1.5, k=32,
+                       theta=0.6, tau_ref=0.05, bucket=8):
+    """Sub-bucket particle trace test: uniform particles of equal volume 1/N (the
+    weights m/rho), lognormal absorption (sigma_ln=1.5, correlation length 0.05) so
+    that buckets hold very different particles, smoothing lengths from the 32nd
+    neighbour, uniform sources."""
+    rng = np.random.default_rng(seed)
+    gas = _unit_positions(rng, n_gas)
+    a = lognormal_alpha(rng, gas, alpha0, sigma, 0.05)
+    src = _unit_positions(rng, n_src)
+    lum = rng.lognormal(0.0, 1.0, n_src).astype(np.float32)
+    w = np.full(n_gas, 1.0 / n_gas, dtype=np.float32)
+    return _problem(f"subbucket_{n_gas}_{n_src}", gas, a, src, lum, theta, tau_ref, bucket,
+                    weight=w, seed=seed, hsml=knn_smoothing(gas, k))
+
+
 def sink_sample(n_gas, n_sample, seed=7):
     """A seeded sample of sink indices (sorted, without repetition)."""
     rng = np.random.default_rng(seed)
