@@ -154,6 +154,20 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def _cpu_model():
+    """The host CPU's model name (lscpu), or the platform's description."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
 def _oracle_baseline(P, n_gas, sample_n, seconds, seed=7):
     """Time the FP64 oracle as it stands on the host cores on a bounded sample: the
     full tree build, the flux at `sample_n` seeded sinks (also the parity sample),
@@ -178,6 +192,7 @@ def _oracle_baseline(P, n_gas, sample_n, seconds, seed=7):
     # build time is charged in proportion to the sample's share of the sinks
     per_sink = t_walk / m + t_build / n_gas
     info = {"value": 1.0 / per_sink, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu": _cpu_model(),
             "sample": f"{m} of {n_gas} sinks walked (seeded) + the full {n_gas}-particle "
                       f"tree build charged pro rata; walk {t_walk:.2f} s, build {t_build:.2f} s",
             "walk_s": t_walk, "build_s": t_build}
@@ -218,7 +233,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": _config(P, args.workload, desc),
-            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT,
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "cpu": _cpu_model(),
+                             "value": value, "unit": UNIT,
                              "sample": f"each step walks {sample_n} seeded sinks of {n}; the "
                                        f"{n}-particle tree build ({t_build:.2f} s, once) is "
                                        f"charged pro rata"},
@@ -555,7 +571,8 @@ def run_ours(args):
         fg = flux.cpu().numpy()[sinks].astype(np.float64)
         big = fo >= 1e-30
         rel = np.abs(fg[big] - fo[big]) / fo[big]
-        line["cpu_baseline"] = {k: info[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline"] = {k: info[k] for k in ("value", "unit", "cores", "kind", "sample",
+                                                      "cpu")}
         line["parity"] = {"sinks": int(len(sinks)), "median_rel_err": float(np.median(rel)),
                           "max_rel_err": float(rel.max()),
                           "pass": bool(np.median(rel) <= 1e-5 and rel.max() <= 1e-3)}

@@ -14,20 +14,25 @@
 // The decisions (opening angle, refinement, "does the ray touch the cell") are
 // evaluated with explicitly rounded fp32 operations in a fixed order.
 //
-// GPU form.
-//   * One lane per sink, sinks in Morton order: the lanes of a warp are
-//     neighbours in space and visit almost the same cells.
-//   * Each lane runs a flat loop; one iteration is one walk step or one cell
-//     clip (the clips dominate: thousands per sink). The clip iteration picks
-//     its cell with selects from one per-lane list (sink ancestors | walk path
-//     | refinement stack), so lanes on different kinds of cells stay converged.
-//   * A warp owns a chunk of consecutive sinks; a lane that finishes its sink
-//     takes the next one of the chunk (ballot), so no lane idles while the
-//     warp's slowest sink finishes.
+// GPU form (sinks in Morton order, so the lanes of a warp are neighbours in space).
+//   * Variant 1 (walk_kernel): one lane per sink, a flat loop in which one
+//     iteration is a walk step or a cell clip, cells picked with selects from one
+//     per-lane list; a lane that finishes takes the next sink of its warp's chunk.
+//   * Variant 2 (walk_warp_kernel, MERGE = false): the 32 lanes walk one shared
+//     stack in shared memory with a mask of the lanes that still need each cell,
+//     and trace together the rays to a cell they accept together.
+//   * Variant 3 (MERGE = true, the default): as 2, but a lane keeps its next ray
+//     pending, and the pending rays of all lanes (to different cells) are traced
+//     together, so more lanes share each traced step.
 //   * The segment cells of a ray are known without following parent links: the
 //     sibling of a cell is its index XOR 1 (children are allocated in pairs) and
 //     the common ancestor's depth is the length of the common prefix of the
-//     sink's ancestor list and the walk path, kept as a 64-bit mask.
+//     sink's ancestor list and the walk path, kept as a 64-bit mask. Refined
+//     children are clipped after the ray's base segments.
+// Template options of the warp walk: ADJ (adjoint accumulation, Sec. 2.2 with the
+// decisions frozen), MOM (flux vector and pressure moments), BG (background
+// sources moved onto a sphere), STOP (early ray termination), NB (several bands)
+// and SUB (sub-bucket particle trace).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -600,43 +605,110 @@ __device__ __forceinline__ float gl6(float b2, float a, float c, float invh) {
   return acc * hw;
 }
 
-// integral of W over u in [0, s] (s >= 0), W normalised by 1/(pi h^3)
-__device__ __forceinline__ float kernel_half(float b2, float s, float H, float invh) {
-  const float h2 = H * H;
-  const float u1 = b2 < h2 ? sqrtf(h2 - b2) : 0.0f;
-  const float u2 = b2 < 4.0f * h2 ? sqrtf(4.0f * h2 - b2) : 0.0f;
-  const float a1 = fminf(s, u1), a2 = fminf(s, u2);
-  return (gl6(b2, 0.0f, a1, invh) + gl6(b2, a1, a2, invh)) * (invh * invh * invh * 0.318309886f);
-}
-
+// integral of W(sqrt(b^2 + u^2), h) du over [s0, s1], split at the break points
+// u = 0, +-u1 (r = h) and +-u2 (r = 2h) and cut to the support |u| < u2
 __device__ __forceinline__ float kernel_line(float b2, float s0, float s1, float H) {
   const float invh = 1.0f / H;
-  const float g1 = s1 >= 0.0f ? kernel_half(b2, s1, H, invh) : -kernel_half(b2, -s1, H, invh);
-  const float g0 = s0 >= 0.0f ? kernel_half(b2, s0, H, invh) : -kernel_half(b2, -s0, H, invh);
-  return g1 - g0;
+  const float h2 = H * H;
+  const float u1 = b2 < h2 ? sqrtf(h2 - b2) : 0.0f;
+  const float u2 = sqrtf(fmaxf(4.0f * h2 - b2, 0.0f));
+  float lo = fmaxf(s0, -u2);
+  const float hi = fminf(s1, u2);
+  float acc = 0.0f;
+  const float brk[4] = {-u1, 0.0f, u1, u2};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float c = fminf(brk[k], hi);
+    if (c > lo) {
+      acc += gl6(b2, lo, c, invh);
+      lo = c;
+    }
+  }
+  return acc * (invh * invh * invh * 0.318309886f);
 }
 
-// optical depth of the chord p + t d, t in [t0, t1], through the particles listed for
-// leaf `box`, the receiving particle (sorted index si) left out
-__device__ float sub_bucket_tau(const TreeView& T, int box, int si, float px, float py, float pz,
-                                float dx, float dy, float dz, float s2, float len, float t0,
-                                float t1) {
-  CSum acc;
-  const unsigned k1 = __ldg(&T.nbr_first[box + 1]);
-  for (unsigned k = __ldg(&T.nbr_first[box]); k < k1; ++k) {
-    const int j = __ldg(&T.nbr[k]);
-    if (j == si) continue;
-    const float a = __ldg(&T.aw[j]);
-    if (!(a > 0.0f)) continue;
-    const float4 q = __ldg(&T.sp[j]);
-    const float ux = q.x - px, uy = q.y - py, uz = q.z - pz;
-    const float tc = (ux * dx + uy * dy + uz * dz) / s2;
-    const float ex = ux - tc * dx, ey = uy - tc * dy, ez = uz - tc * dz;
-    const float b2 = ex * ex + ey * ey + ez * ez;
-    if (b2 >= 4.0f * q.w * q.w) continue;
-    acc.add(a * kernel_line(b2, (t0 - tc) * len, (t1 - tc) * len, q.w));
+// Per-warp queue of the neighbours whose support meets the chord, so that the
+// quadrature runs on full warps: (b^2, s0, s1, h) and the absorbing mass.
+struct SubQueue {
+  float4 g[64];
+  float a[64];
+};
+
+// Optical depth of lane src's chord p + t d, t in [t0, t1], through the particles
+// listed for its leaf, the receiving particle (sorted index si) left out. The 32
+// lanes of the warp test one neighbour each per round; the neighbours that reach
+// the chord are queued in shared memory and integrated 32 at a time. Every lane
+// must call it; all lanes return the sum.
+__device__ __forceinline__ float sub_bucket_tau_warp(const TreeView& T, int src, int box, int si,
+                                                     float px, float py, float pz, float dx,
+                                                     float dy, float dz, float s2, float len,
+                                                     float t0, float t1) {
+  const unsigned FULL = 0xffffffffu;
+  const unsigned lane = threadIdx.x & 31u;
+  __shared__ SubQueue queues[4];  // one per warp of a 128-thread block
+  SubQueue& Q = queues[threadIdx.x >> 5];
+  box = __shfl_sync(FULL, box, src);
+  si = __shfl_sync(FULL, si, src);
+  px = __shfl_sync(FULL, px, src);
+  py = __shfl_sync(FULL, py, src);
+  pz = __shfl_sync(FULL, pz, src);
+  dx = __shfl_sync(FULL, dx, src);
+  dy = __shfl_sync(FULL, dy, src);
+  dz = __shfl_sync(FULL, dz, src);
+  s2 = __shfl_sync(FULL, s2, src);
+  len = __shfl_sync(FULL, len, src);
+  t0 = __shfl_sync(FULL, t0, src);
+  t1 = __shfl_sync(FULL, t1, src);
+  float part = 0.0f;
+  int qn = 0;  // queued entries (warp-uniform)
+  const unsigned k0 = __ldg(&T.nbr_first[box]), k1 = __ldg(&T.nbr_first[box + 1]);
+  for (unsigned base = k0; base < k1; base += 32u) {
+    const unsigned k = base + lane;
+    bool pass = false;
+    float a = 0.0f, b2 = 0.0f, sa = 0.0f, sb = 0.0f, H = 1.0f;
+    if (k < k1) {
+      const int j = __ldg(&T.nbr[k]);
+      a = __ldg(&T.aw[j]);
+      if (j != si && a > 0.0f) {
+        const float4 q = __ldg(&T.sp[j]);
+        const float ux = q.x - px, uy = q.y - py, uz = q.z - pz;
+        const float tc = (ux * dx + uy * dy + uz * dz) / s2;
+        const float ex = ux - tc * dx, ey = uy - tc * dy, ez = uz - tc * dz;
+        b2 = ex * ex + ey * ey + ez * ez;
+        H = q.w;
+        sa = (t0 - tc) * len;
+        sb = (t1 - tc) * len;
+        const float R2 = 4.0f * H * H;
+        if (b2 < R2) {  // the chord [sa, sb] must meet the support |s| < u2
+          const float u2 = sqrtf(R2 - b2);
+          pass = sb > -u2 && sa < u2;
+        }
+      }
+    }
+    const unsigned m = __ballot_sync(FULL, pass);
+    if (pass) {
+      const int at = qn + __popc(m & ((1u << lane) - 1u));
+      Q.g[at] = make_float4(b2, sa, sb, H);
+      Q.a[at] = a;
+    }
+    qn += __popc(m);
+    __syncwarp();
+    if (qn >= 32) {
+      const int at = qn - 32 + (int)lane;
+      const float4 g = Q.g[at];
+      part += Q.a[at] * kernel_line(g.x, g.y, g.z, g.w);
+      qn -= 32;
+      __syncwarp();
+    }
   }
-  return acc.get();
+  if ((int)lane < qn) {
+    const float4 g = Q.g[lane];
+    part += Q.a[lane] * kernel_line(g.x, g.y, g.z, g.w);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+  return part;
 }
 
 // Rays from the sinks of the lanes in `on` to (q, L) inside cell C; every lane
@@ -659,7 +731,7 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
                                          SinkCounters& cnt, CSum* F, Moments* mom,
                                          const int si = -1) {
   static_assert(NB == 1 || NB == 2 || NB == 4, "band slots: 1, 2 or 4");
-  static_assert(!SUB || (!ADJ && !MOM && NB == 1), "sub-bucket trace: plain flux only");
+  static_assert(!SUB || (!ADJ && !MOM && !STOP && NB == 1), "sub-bucket trace: plain flux only");
   static_assert(NB == 1 || !(ADJ || MOM || STOP), "bands: plain flux only");
   const unsigned FULL = 0xffffffffu;
   float dx = 0.0f, dy = 0.0f, dz = 0.0f, s2 = 1.0f, len = 1.0f, ix = 0.0f, iy = 0.0f, iz = 0.0f;
@@ -700,6 +772,9 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
   int nseg = 0, kk = 0;
   bool seg_over = false;
   float gq0 = 0.0f, gq1 = 0.0f, gq2 = 0.0f, fcur = 0.0f;
+  bool need_sub = false;  // (SUB) this step's leaf is traced through its particles
+  int sub_box = 0;
+  float sub_t0 = 0.0f, sub_t1 = 0.0f;
   while (__any_sync(FULL, active)) {
     int akey = -1;
     float aval = 0.0f;
@@ -832,8 +907,12 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
                   }
                 } else if (SUB && (P.tau_ref <= 0.0f ||
                                    __fmul_rn(__ldg(&T.dbk[box]), l) > P.tau_ref)) {
-                  // a bucket that still asks for refinement: trace its particles
-                  tau.add(sub_bucket_tau(T, box, si, px, py, pz, dx, dy, dz, s2, len, t0, t1));
+                  // a bucket that still asks for refinement: its particles are traced
+                  // by the whole warp at the end of this step
+                  need_sub = true;
+                  sub_box = box;
+                  sub_t0 = t0;
+                  sub_t1 = t1;
                   ++cnt.sub;
                 } else {
                   tau.add(a.w * l);
@@ -867,6 +946,18 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
           }
         }
       }
+    }
+    if (SUB) {
+      // the leaves of this step that need the particle trace, one after another
+      unsigned m = __ballot_sync(FULL, need_sub);
+      while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1u;
+        const float t = sub_bucket_tau_warp(T, src, sub_box, si, px, py, pz, dx, dy, dz, s2, len,
+                                            sub_t0, sub_t1);
+        if ((int)(threadIdx.x & 31u) == src) tau.add(t);
+      }
+      need_sub = false;
     }
     if (ADJ) warp_atomic_add(J.G, akey, aval);
   }
