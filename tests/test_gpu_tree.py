@@ -28,7 +28,22 @@ def _cases():
     # a single particle
     P4 = workloads.uniform_box(n_gas=1, n_src=1, seed=8)
     return [("uniform4096", P0), ("lognormal_weighted", P1), ("clustered_dups", P2),
-            ("shifted_domain", P3), ("single", P4)]
+            ("shifted_domain", P3), ("single", P4), ("deep", deep_problem())]
+
+
+def deep_problem():
+    """A comb of 64 particles whose Morton keys are 0 and every single bit 2^b
+    (the point with only grid bit m of one axis set), in buckets of one: each
+    level of the tree splits off one particle, down to depth 63."""
+    P = workloads.uniform_box(n_gas=64, n_src=40, seed=12, bucket=1)
+    g = np.zeros((3, 64), np.float32)
+    k = 1
+    for m in range(21):
+        for axis in range(3):
+            g[axis, k] = np.float32(2.0 ** (m - 21))
+            k += 1
+    P["gas_xyz"] = g
+    return P
 
 
 @pytest.mark.parametrize("name,P", _cases(), ids=[c[0] for c in _cases()])
@@ -85,3 +100,18 @@ def test_out_of_domain_and_invalid_inputs():
     # the context is still usable afterwards
     G = gpu_tree(P)
     assert G.n_nodes > 0
+
+
+def test_deep_tree_flux():
+    # the walk and the rays at the full tree depth (cells 63 levels down)
+    from paper_1902_08083_gb300 import trevr
+    from _parity import assert_flux_parity
+    P = deep_problem()
+    G = gpu_tree(P)
+    T = oracle_tree(P)
+    assert G.max_depth == 63
+    for theta, tau_ref in ((0.75, 0.1), (0.0, 0.0)):
+        f, c = trevr.compute_flux(G, theta, tau_ref, counters=True)
+        of, oc, _ = T.flux(theta, tau_ref, with_counters=True)
+        assert_flux_parity(f.cpu().numpy(), of, f"deep tree theta={theta}")
+        assert np.count_nonzero(np.any(c.cpu().numpy() != oc.astype(np.int32), axis=1)) <= 2
