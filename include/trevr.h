@@ -135,8 +135,9 @@ int trevr_build_tree(const float* gas_xyz, const float* alpha, const float* weig
 
 /*
  * Flux at the sinks (Eq. simpint summed over the pseudo-sources of the
- * opening-angle walk, Sec. 2.2.1-2.2.3), in fp32 with the optical depth
- * accumulated by compensated summation.
+ * opening-angle walk, Sec. 2.2.1-2.2.3), in fp32. Each sink's flux is a
+ * compensated sum. The warp-shared walks (variants 2 and 3) sum a ray's optical
+ * depth plainly, and the per-lane walk (variant 1) sums it with compensation.
  *
  *   t         tree from trevr_build_tree.
  *   sink_idx  n_sink int64 caller indices of gas particles, or NULL = all
