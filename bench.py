@@ -539,7 +539,7 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     achieved = alg_bytes / t_walk / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "walk_warp_kernel<false, true> (warp-shared walk, merged rays, flux)",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "walk_warp_kernel, variant 3 (warp-shared walk, merged rays, flux)",
                 "peak_kind": f"{peak_kind} (copy bandwidth, burst)",
                 "bytes_per_launch": alg_bytes}
 
