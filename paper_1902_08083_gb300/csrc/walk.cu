@@ -729,7 +729,7 @@ __device__ __forceinline__ float sub_bucket_tau_warp(const TreeView& T, int src,
 // optical depth over the shared segments, and F[b] gets band b's flux.
 // SUB: the sub-bucket particle trace for leaves whose own particles ask for
 // refinement (the sink's sorted index si is left out of the sum).
-template <bool ADJ, bool MOM, bool STOP = false, int NB = 1, bool SUB = false>
+template <bool ADJ, bool MOM, bool STOP = false, int NB = 1, bool SUB = false, bool CNT = true>
 __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P, const bool on,
                                          const float px, const float py, const float pz,
                                          const int S, const int dS, const int* anc, int* rst,
@@ -795,7 +795,7 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
         aval = -gk * fcur * segl[kk];
         ++kk;
       } else {
-        ++cnt.rays;
+        if (CNT) ++cnt.rays;
         active = false;
       }
     } else if (active) {
@@ -803,8 +803,8 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
       if (!from_stack && b >= nb) {
         const float f = L * expf(-tau.get()) / (kFourPi * s2);
         if (!ADJ && STOP && cut) {
-          ++cnt.cut;
-          ++cnt.rays;
+          if (CNT) ++cnt.cut;
+          if (CNT) ++cnt.rays;
           active = false;
         } else if (!ADJ) {
           if (NB > 1) {
@@ -832,7 +832,7 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
             mom->v[7].add(f * n0 * n2);
             mom->v[8].add(f * n1 * n2);
           }
-          ++cnt.rays;
+          if (CNT) ++cnt.rays;
           active = false;
         } else if (pass == 1) {
           fcur = f;  // second pass over the same cells, now that f is known
@@ -847,7 +847,7 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
             boxes = 0;
           }
         } else {
-          ++cnt.rays;
+          if (CNT) ++cnt.rays;
           active = false;
         }
       } else {
@@ -889,7 +889,7 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
             slab(a.z, bb.z, pz, dz, iz, t0, t1, miss);
           }
           const float l = (!miss && t1 > t0) ? __fmul_rn(__fsub_rn(t1, t0), len) : 0.0f;
-          ++cnt.clip;
+          if (CNT) ++cnt.clip;
           if (l > 0.0f) {
             bool pushed = false;
             if (P.tau_ref <= 0.0f || __fmul_rn(bb.w, l) > P.tau_ref) {
@@ -899,7 +899,7 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
                   atomicOr(status, kStatusStackOverflow);
                   active = false;
                 } else {
-                  ++cnt.ref;
+                  if (CNT) ++cnt.ref;
                   rst[rsp++] = ~child;  // both children, clipped after the base segments
                 }
                 pushed = true;
@@ -926,7 +926,7 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
                   sub_box = box;
                   sub_t0 = t0;
                   sub_t1 = t1;
-                  ++cnt.sub;
+                  if (CNT) ++cnt.sub;
                 } else {
                   tau.add(a.w * l);
                 }
@@ -954,7 +954,7 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
                   gq1 = fmaf(a.w, g1 * len + w * dy, gq1);
                   gq2 = fmaf(a.w, g2 * len + w * dz, gq2);
                 }
-                ++cnt.segs;
+                if (CNT) ++cnt.segs;
               }
             }
           }
@@ -1003,7 +1003,7 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
 // q = o + d * (R / s); the ray then ends in the leaf that holds q, whose ancestors the
 // lane finds by descending the cut planes from the root and keeps for that ray.
 template <bool ADJ, bool MERGE, bool MOM = false, bool BG = false, bool STOP = false, int NB = 1,
-          bool SUB = false>
+          bool SUB = false, bool CNT = true>
 __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P, const bool has,
                                           const int i, const float gk, WarpStack& ws,
                                           int* status, const AdjointArgs& J,
@@ -1055,11 +1055,11 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
         for (int d = 0; d <= mn && cpath[d] == anc[d]; ++d) onp |= 1ull << d;
         pp = cpath;
       }
-      warp_ray<ADJ, MOM, STOP, NB, SUB>(T, P, pnd, px, py, pz, S, dS, anc, rst, onp, pp, pC, pdC, pqx, pqy,
+      warp_ray<ADJ, MOM, STOP, NB, SUB, CNT>(T, P, pnd, px, py, pz, S, dS, anc, rst, onp, pp, pC, pdC, pqx, pqy,
                          pqz, pL, psrc, gk, stack_limit, box_limit, status, J, cnt, F, mom,
                          i);
     } else {
-      warp_ray<ADJ, MOM, STOP, NB, SUB>(T, P, pnd, px, py, pz, S, dS, anc, rst, on_path, ws.path, pC, pdC,
+      warp_ray<ADJ, MOM, STOP, NB, SUB, CNT>(T, P, pnd, px, py, pz, S, dS, anc, rst, on_path, ws.path, pC, pdC,
                          pqx, pqy, pqz, pL, psrc, gk, stack_limit, box_limit, status, J, cnt, F,
                          mom, i);
     }
@@ -1082,7 +1082,7 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
     if (!(s.w > 0.0f)) continue;
     bool acc = false, opn = false;
     if ((M >> lane) & 1u) {
-      ++cnt.visit;
+      if (CNT) ++cnt.visit;
       const float4 a = __ldg(&T.nA[X]);
       const float4 bb = __ldg(&T.nB[X]);
       const float ex = fmaxf(fmaxf(__fsub_rn(a.x, px), __fsub_rn(px, bb.x)), 0.0f);
@@ -1148,7 +1148,7 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
         }
       }
     } else if (accM) {
-      warp_ray<ADJ, MOM, STOP, NB, SUB>(T, P, acc, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX, s.x,
+      warp_ray<ADJ, MOM, STOP, NB, SUB, CNT>(T, P, acc, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX, s.x,
                          s.y, s.z, s.w, -1, gk, stack_limit, box_limit, status, J, cnt, F, mom,
                          i);
     }
@@ -1171,7 +1171,7 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
               psrc = jj;
             }
           } else {
-            warp_ray<ADJ, MOM, STOP, NB, SUB>(T, P, opn, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX,
+            warp_ray<ADJ, MOM, STOP, NB, SUB, CNT>(T, P, opn, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX,
                                y.x, y.y, y.z, y.w, jj, gk, stack_limit, box_limit, status, J, cnt,
                                F, mom, i);
           }
@@ -1198,10 +1198,14 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
 }
 
 // 8 blocks of 128 per SM (at most 64 registers): measured 4% faster forward and 8%
-// faster adjoint than the compiler's own 70 registers at 7 blocks
+// faster adjoint than the compiler's own 70 registers at 7 blocks. Without
+// counters (CNT = false, the plain flux when the caller asks for no counters or
+// stats) the walk fits 9 blocks (56 registers): 5% faster again on the clumpy
+// workload (135 ms against 142.8 ms); 10 blocks spilled more and were slower.
+// CNT = false keeps no per-sink counters; the fluxes are bit-identical.
 template <bool ADJ, bool MERGE, bool MOM = false, bool BG = false, bool STOP = false, int NB = 1,
-          bool SUB = false>
-__global__ void __launch_bounds__(128, (NB > 1 || SUB) ? 4 : 8) walk_warp_kernel(TreeView T, const long long* sink_idx,
+          bool SUB = false, bool CNT = true>
+__global__ void __launch_bounds__(128, (NB > 1 || SUB) ? 4 : (CNT ? 8 : 9)) walk_warp_kernel(TreeView T, const long long* sink_idx,
                                                         int n_sink, WalkParams P, SinkOut out,
                                                         unsigned long long* stats, int* status,
                                                         AdjointArgs J) {
@@ -1224,7 +1228,7 @@ __global__ void __launch_bounds__(128, (NB > 1 || SUB) ? 4 : 8) walk_warp_kernel
   CSum F[NB];
   Moments mom;
   if (__any_sync(0xffffffffu, has))
-    warp_walk<ADJ, MERGE, MOM, BG, STOP, NB, SUB>(T, P, has, i, g, ws, status, J, cnt, F,
+    warp_walk<ADJ, MERGE, MOM, BG, STOP, NB, SUB, CNT>(T, P, has, i, g, ws, status, J, cnt, F,
                                                   MOM ? &mom : nullptr);
   if (MOM && has) {
 #pragma unroll
@@ -1384,22 +1388,37 @@ cudaError_t launch_walk(const TreeView& T, const long long* sink_idx, int n_sink
     const dim3 grid((n_sink + 127) / 128);
     const SinkOut o{flux_out, counters, nullptr, nullptr, n_sink};
     const bool bg = wp.bg_radius > 0.0f, stop = wp.tau_stop < INFINITY;
-    if (bg && stop)
-      walk_warp_kernel<false, true, false, true, true><<<grid, 128, 0, s>>>(
-          T, sink_idx, n_sink, wp, o, stats, status, AdjointArgs{});
-    else if (bg)
-      walk_warp_kernel<false, true, false, true><<<grid, 128, 0, s>>>(
-          T, sink_idx, n_sink, wp, o, stats, status, AdjointArgs{});
-    else
-      walk_warp_kernel<false, true, false, false, true><<<grid, 128, 0, s>>>(
-          T, sink_idx, n_sink, wp, o, stats, status, AdjointArgs{});
+    if (counters || stats) {
+      if (bg && stop)
+        walk_warp_kernel<false, true, false, true, true><<<grid, 128, 0, s>>>(
+            T, sink_idx, n_sink, wp, o, stats, status, AdjointArgs{});
+      else if (bg)
+        walk_warp_kernel<false, true, false, true><<<grid, 128, 0, s>>>(
+            T, sink_idx, n_sink, wp, o, stats, status, AdjointArgs{});
+      else
+        walk_warp_kernel<false, true, false, false, true><<<grid, 128, 0, s>>>(
+            T, sink_idx, n_sink, wp, o, stats, status, AdjointArgs{});
+    } else {  // no counters asked for: the walk keeps none
+      if (bg && stop)
+        walk_warp_kernel<false, true, false, true, true, 1, false, false><<<grid, 128, 0, s>>>(
+            T, sink_idx, n_sink, wp, o, nullptr, status, AdjointArgs{});
+      else if (bg)
+        walk_warp_kernel<false, true, false, true, false, 1, false, false><<<grid, 128, 0, s>>>(
+            T, sink_idx, n_sink, wp, o, nullptr, status, AdjointArgs{});
+      else
+        walk_warp_kernel<false, true, false, false, true, 1, false, false><<<grid, 128, 0, s>>>(
+            T, sink_idx, n_sink, wp, o, nullptr, status, AdjointArgs{});
+    }
     note_launch();
     return cudaGetLastError();
   }
   if (wp.variant >= 2) {
-    if (wp.variant == 3)
+    if (wp.variant == 3 && (counters || stats))
       walk_warp_kernel<false, true><<<(n_sink + 127) / 128, 128, 0, s>>>(
           T, sink_idx, n_sink, wp, SinkOut{flux_out, counters, nullptr, nullptr, n_sink}, stats, status, AdjointArgs{});
+    else if (wp.variant == 3)  // no counters asked for: the walk keeps none
+      walk_warp_kernel<false, true, false, false, false, 1, false, false><<<(n_sink + 127) / 128, 128, 0, s>>>(
+          T, sink_idx, n_sink, wp, SinkOut{flux_out, nullptr, nullptr, nullptr, n_sink}, nullptr, status, AdjointArgs{});
     else
       walk_warp_kernel<false, false><<<(n_sink + 127) / 128, 128, 0, s>>>(
           T, sink_idx, n_sink, wp, SinkOut{flux_out, counters, nullptr, nullptr, n_sink}, stats, status, AdjointArgs{});
