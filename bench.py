@@ -426,6 +426,44 @@ def _bench_sub_bucket(args):
             "median_rel_change": float(rel.median())}
 
 
+def _bench_glass(args):
+    """The perturbed-glass stand-in at the paper's size (64^3 gas, 64^3 stars;
+    Sec. 3.1, Appendix A): rays and segments per element and the RMS flux error
+    against theta = 0 (512 seeded sinks) and against tau_ref = 1e-8 (every sink),
+    beside the values the paper prints for its glass (Sec. 3.1.2, 3.1.3)."""
+    import torch
+    from paper_1902_08083_gb300 import trevr
+    P = workloads.perturbed_glass(64)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t = {k: torch.from_numpy(np.ascontiguousarray(P[k])).to(dev)
+         for k in ("gas_xyz", "alpha", "src_xyz", "src_lum", "weight")}
+    tree = trevr.build_tree(t["gas_xyz"], t["alpha"], t["src_xyz"], t["src_lum"],
+                            weight=t["weight"], lo=P["lo"], side=P["side"], bucket=P["bucket"])
+    n = tree.n_gas
+    sinks = torch.from_numpy(workloads.sink_sample(n, 512, seed=16)).to(dev)
+
+    def rms(f, ref):
+        return float(torch.sqrt(torch.mean(((f.double() - ref.double()) / ref.double()) ** 2)))
+
+    f0 = trevr.compute_flux(tree, 0.0, 0.1, sink_idx=sinks)
+    theta = {}
+    for th in (0.45, 0.6, 0.75, 1.0):
+        f, st = trevr.compute_flux(tree, th, 0.1, stats=True)
+        theta[str(th)] = {"rays_per_element": st["interactions"] / n,
+                          "rms_error_vs_theta0": rms(f[sinks], f0)}
+    fr = trevr.compute_flux(tree, 0.75, 1e-8)
+    tau = {}
+    for tr in (0.01, 0.1, 1.0, 1e6):
+        f, st = trevr.compute_flux(tree, 0.75, tr, stats=True)
+        tau[str(tr)] = {"segments_per_element": st["segments"] / n,
+                        "rms_error_vs_tau_ref_1e-8": rms(f, fr)}
+    tree.free()
+    return {"workload": "perturbed-glass stand-in, 64^3 gas + 64^3 stars, 24 tabulated modes",
+            "theta_sweep_tau_ref_0.1": theta, "tau_ref_sweep_theta_0.75": tau,
+            "paper_prints": "theta 0.75: 200 rays, 3 %; theta 0.45: 500 rays, 1 %; "
+                            "tau_ref 0.1: 850 segments, 1 % (Sec. 3.1.2, 3.1.3)"}
+
+
 def run_ours(args):
     import torch
     from paper_1902_08083_gb300 import trevr
@@ -565,6 +603,7 @@ def run_ours(args):
         line["terminated"] = _bench_termination(args, P, g)
         line["bands"] = _bench_bands(args, P, g)
         line["sub_bucket"] = _bench_sub_bucket(args)
+        line["glass"] = _bench_glass(args)
 
     if world == 1 and not args.no_cpu_baseline:
         info, sinks, fo, _ = _oracle_baseline(P, n, args.cpu_sample, args.cpu_seconds)

@@ -12,6 +12,8 @@ lognormal absorption field replace them.
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 ONE_BELOW = np.nextafter(np.float32(1.0), np.float32(0.0))
@@ -197,6 +199,50 @@ def sub_bucket_problem(n_gas=1 << 12, n_src=32, seed=11, alpha0=2.0, sigma=1.5, 
     w = np.full(n_gas, 1.0 / n_gas, dtype=np.float32)
     return _problem(f"subbucket_{n_gas}_{n_src}", gas, a, src, lum, theta, tau_ref, bucket,
                     weight=w, seed=seed, hsml=knn_smoothing(gas, k))
+
+
+_GLASS_MODES = os.path.join(os.path.dirname(os.path.abspath(__file__)), "glass_modes.txt")
+
+
+def glass_modes():
+    """The 24 (k_x, k_y, k_z, phi) modes of the perturbed glass (Appendix A, Table
+    "modes" of the paper), shape (24, 4)."""
+    return np.loadtxt(_GLASS_MODES, comments="#")[:, 1:]
+
+
+def perturbed_glass(n_side=64, seed=13, jitter=0.25, k=32, theta=0.75, tau_ref=0.1, bucket=8):
+    """Stand-in for the sinusoidally perturbed glass of the accuracy tests (Sec. 3.1.1,
+    Appendix A). The glass file is not available, so a cubic lattice of n_side^3
+    points with seeded uniform jitter of +-jitter spacings replaces it. Each point
+    moves by (1/275) sin(k_i . r0 + phi_i) along the unit vector of k_i for each of
+    the 24 tabulated modes, and wraps into the unit box (the printed Eq. manfft adds
+    a scalar to a vector; this is its reading). The stars are the gas points with
+    their coordinates cycled (x_s = y_g, y_s = z_g, z_s = x_g), each of luminosity 1.
+    The gas has total mass 1 and opacity 1, so alpha = rho, with the density from the
+    distance to the k-th neighbour, rho_i = k m / ((4/3) pi d_k^3), and the volume
+    weights w_i = m / rho_i."""
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng(seed)
+    n = n_side ** 3
+    g = (np.arange(n_side) + 0.5) / n_side
+    r0 = np.stack(np.meshgrid(g, g, g, indexing="ij")).reshape(3, n)
+    r0 = r0 + rng.uniform(-jitter, jitter, (3, n)) / n_side
+    modes = glass_modes()
+    r = r0.copy()
+    for kx, ky, kz, phi in modes:
+        kv = np.array([kx, ky, kz])
+        r += (np.sin(kv @ r0 + phi) / 275.0) * (kv / np.linalg.norm(kv))[:, None]
+    r = np.mod(r, 1.0)
+    gas = np.minimum(r.astype(np.float32), ONE_BELOW)
+    m = 1.0 / n
+    d, _ = cKDTree(np.mod(r, 1.0).T, boxsize=1.0).query(np.mod(r, 1.0).T, k=k + 1)
+    rho = k * m / (4.0 / 3.0 * np.pi * d[:, -1] ** 3)
+    alpha = rho.astype(np.float32)
+    w = (m / rho).astype(np.float32)
+    src = np.ascontiguousarray(gas[[1, 2, 0]])
+    lum = np.ones(n, np.float32)
+    return _problem(f"glass_{n_side}", gas, alpha, src, lum, theta, tau_ref, bucket, weight=w,
+                    seed=seed)
 
 
 def sink_sample(n_gas, n_sample, seed=7):
