@@ -16,6 +16,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import shutil
 import statistics
 import subprocess
 import sys
@@ -86,14 +87,18 @@ class Clocks:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, keep_dir=None):
+        """keep_dir: also keep the raw samples there as clocks_rank<i>.csv."""
+        import tempfile
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.keep = (None if not keep_dir else
+                     os.path.join(keep_dir, f"clocks_rank{gpu_index}.csv"))
+        fd, self.path = tempfile.mkstemp(prefix="trevr_clocks_", suffix=".csv")
+        os.close(fd)
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
@@ -104,6 +109,8 @@ class Clocks:
 
     def stop(self):
         if self.proc is None:
+            if os.path.exists(self.path):
+                os.remove(self.path)
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         try:
@@ -125,6 +132,10 @@ class Clocks:
             for n, v in zip(names, parts[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
+        if self.keep:
+            os.makedirs(os.path.dirname(os.path.abspath(self.keep)), exist_ok=True)
+            shutil.copyfile(self.path, self.keep)
+        os.remove(self.path)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
@@ -504,7 +515,7 @@ def run_ours(args):
         step().free()
     torch.cuda.synchronize()
 
-    clocks = Clocks(local)
+    clocks = Clocks(local, args.clocks_dir)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -654,6 +665,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="clumpy", choices=["clumpy", "stromgren", "uniform"])
     ap.add_argument("--cpu-sample", type=int, default=2048)
+    ap.add_argument("--clocks-dir", default=None,
+                    help="directory in which to keep the raw nvidia-smi clock samples")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="seconds of oracle walking timed for cpu_baseline")
     ap.add_argument("--ref-seconds", type=float, default=90.0,
