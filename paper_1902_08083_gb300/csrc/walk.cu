@@ -1255,8 +1255,10 @@ __global__ void __launch_bounds__(128, (NB > 1 || SUB) ? 4 : (CNT ? 8 : 9)) walk
 
 // Batched form of the warp-shared walk: each work item is cut into groups of 32
 // consecutive sinks, one warp walk per group.
-template <int BS, bool MERGE>
-__global__ void __launch_bounds__(BS, 1024 / BS) walk_warp_batched_kernel(
+// CNT = false (no stats asked for): no counters, and 9 blocks-of-128 worth of
+// threads per SM instead of 8, as for the single-tree walk.
+template <int BS, bool MERGE, bool CNT = true>
+__global__ void __launch_bounds__(BS, CNT ? 1024 / BS : 1152 / BS) walk_warp_batched_kernel(
     const TreeView* __restrict__ views, float* const* __restrict__ flux_out,
     const int2* __restrict__ items, int n_items, int item, unsigned* counter, WalkParams P,
     unsigned long long* stats, int* status) {
@@ -1280,16 +1282,19 @@ __global__ void __launch_bounds__(BS, 1024 / BS) walk_warp_batched_kernel(
       const bool has = i < end;
       SinkCounters cnt;
       CSum F;
-      warp_walk<false, MERGE>(T, Pt, has, i, 0.0f, ws, status, AdjointArgs{}, cnt, &F);
+      warp_walk<false, MERGE, false, false, false, 1, false, CNT>(T, Pt, has, i, 0.0f, ws, status,
+                                                                 AdjointArgs{}, cnt, &F);
       if (has) flux_out[w.x][T.perm[i]] = F.get();
-      tot.rays += cnt.rays;
-      tot.segs += cnt.segs;
-      tot.visit += cnt.visit;
-      tot.ref += cnt.ref;
-      tot.clip += cnt.clip;
+      if (CNT) {
+        tot.rays += cnt.rays;
+        tot.segs += cnt.segs;
+        tot.visit += cnt.visit;
+        tot.ref += cnt.ref;
+        tot.clip += cnt.clip;
+      }
     }
   }
-  if (stats) add_stats(tot, stats);
+  if (CNT && stats) add_stats(tot, stats);
 }
 
 cudaError_t launch_walk_batched(const TreeView* views, float* const* flux_out, const int2* items,
@@ -1305,10 +1310,17 @@ cudaError_t launch_walk_batched(const TreeView* views, float* const* flux_out, c
     const bool merge = wp.variant == 3;
 #define TREVR_WB(BSV, MV)                                                                     \
   do {                                                                                         \
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_warp_batched_kernel<BSV, MV>, \
-                                                  BSV, 0);                                     \
-    walk_warp_batched_kernel<BSV, MV><<<n_sm * per_sm, BSV, 0, s>>>(                          \
-        views, flux_out, items, n_items, item, counter, wp, stats, status);                    \
+    if (stats) {                                                                               \
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_warp_batched_kernel<BSV, MV>, \
+                                                    BSV, 0);                                   \
+      walk_warp_batched_kernel<BSV, MV><<<n_sm * per_sm, BSV, 0, s>>>(                        \
+          views, flux_out, items, n_items, item, counter, wp, stats, status);                  \
+    } else {                                                                                   \
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                           \
+          &per_sm, walk_warp_batched_kernel<BSV, MV, false>, BSV, 0);                          \
+      walk_warp_batched_kernel<BSV, MV, false><<<n_sm * per_sm, BSV, 0, s>>>(                 \
+          views, flux_out, items, n_items, item, counter, wp, nullptr, status);                \
+    }                                                                                          \
   } while (0)
     if (bs == 64) {
       if (merge) TREVR_WB(64, true);
