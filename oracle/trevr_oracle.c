@@ -26,6 +26,20 @@
  * the uniform-medium closed form L exp(-alpha r)/(4 pi r^2) (Eqs. ient,
  * simpint); an opaque occluder casts a shadow; hand-worked alpha_min /
  * alpha_max and cell-density examples; tiling of space by the leaves.
+ * Beyond the flux:
+ *   - the adjoint: finite differences of a replayed frozen forward pass;
+ *   - the moments: direct sums, the trace identity and a single-source
+ *     direction;
+ *   - background sources: the shell formula (Eq. cosmof), and moved sources
+ *     that lie on the sphere;
+ *   - early termination: a closed form, the interaction-list definition and
+ *     the exp(-tau_stop) bound;
+ *   - bands: one band, proportional bands, full refinement and a
+ *     transparent band;
+ *   - the sub-bucket trace: a tree-free line integral of the SPH field, the
+ *     kernel column and an opaque sink.
+ * The glass stand-in is checked against the cost and error ratios that the
+ * paper prints (Sec. 3.1.2, 3.1.3).
  */
 #include <stdint.h>
 #include <stdlib.h>
