@@ -63,3 +63,15 @@ def canonical_nodes_gpu(E):
 def canonical_nodes_oracle(N):
     order = np.lexsort((-N["count"], N["first"]))
     return order
+
+
+_CLUMPY = {}
+
+
+def clumpy_problem():
+    """The clumpy workload at the benchmark's size (2^22 gas, 2^14 sources), generated
+    once per test process (it takes tens of seconds on the host)."""
+    import workloads
+    if "P" not in _CLUMPY:
+        _CLUMPY["P"] = workloads.clumpy()
+    return _CLUMPY["P"]

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import workloads
-from _parity import assert_flux_parity, gpu_tree, oracle_tree
+from _parity import assert_flux_parity, clumpy_problem, gpu_tree, oracle_tree
 
 pytestmark = pytest.mark.gpu
 
@@ -68,13 +68,8 @@ def test_weighted_cells_and_sink_subset(variant):
     np.testing.assert_array_equal(c, rc.astype(np.int32))
 
 
-_CLUMPY = {}
-
-
 def _clumpy():
-    if "P" not in _CLUMPY:
-        _CLUMPY["P"] = workloads.clumpy()
-    return _CLUMPY["P"]
+    return clumpy_problem()
 
 
 @pytest.mark.parametrize("tau_ref", [0.01, 0.1, 0.5])
