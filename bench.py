@@ -5,8 +5,14 @@ One step = build the radiation tree from the particles (keys, sort, topology,
 source deposit, cell moments) + the flux at every sink (source walk, reverse
 rays with tau_ref refinement, flux sum), on inputs already resident in HBM.
 
-Prints one JSON line (rank 0). See the design doc for the workloads, the roofline
-arithmetic and the CPU baseline.
+Prints one JSON line (rank 0). The default workload is the clumpy medium: 2^22
+gas particles with a lognormal absorption field (sigma_ln = 2, correlation
+length 0.05) and a x1e3 cube occluder, 2^14 sources in 16 Gaussian clumps,
+theta_open = 0.6, tau_ref = 0.1, bucket 8. The roofline of the sink walk is its
+instruction issue rate against the SMs' issue limit (the walk is issue-bound,
+with cell records served from L1/L2); the logical bytes of cell records it
+reads per second are reported beside it. cpu_baseline is the FP64 oracle on the
+host cores, on a seeded sample of sinks.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload clumpy|stromgren|uniform]
     python bench.py --impl reference ...   # the FP64 CPU oracle as the reference arm
@@ -338,7 +344,7 @@ def _bench_adjoint(args):
 
 
 def _bench_termination(args, P, g):
-    """Early ray termination (Sec. 5) on an optically thick copy of the workload: the
+    """Early ray termination (Sec. 4) on an optically thick copy of the workload: the
     same particles and sources with every absorption coefficient x16. Times the walk
     with and without tau_stop = 10 and checks the bound 0 <= F - F_stop <=
     exp(-tau_stop) F(alpha = 0) at every sink."""
@@ -376,7 +382,7 @@ def _bench_termination(args, P, g):
 def _bench_bands(args, P, g):
     """Four bands on the workload's particles and sources (absorption x1, x1/2, x1/4, x2;
     luminosity factors 1/2, 1/4, 1/8, 1/8): the band walk against the single-band walk
-    of band 0 (Sec. 5 expects a small constant factor)."""
+    of band 0 (Sec. 4 expects a small constant factor)."""
     import torch
     from paper_1902_08083_gb300 import trevr
     stream = torch.cuda.current_stream()
@@ -614,7 +620,8 @@ def run_ours(args):
         line["terminated"] = _bench_termination(args, P, g)
         line["bands"] = _bench_bands(args, P, g)
         line["sub_bucket"] = _bench_sub_bucket(args)
-        line["glass"] = _bench_glass(args)
+        if args.glass:
+            line["glass"] = _bench_glass(args)
 
     if world == 1 and not args.no_cpu_baseline:
         info, sinks, fo, _ = _oracle_baseline(P, n, args.cpu_sample, args.cpu_seconds)
@@ -674,6 +681,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched (64 boxes) and adjoint (2^21) measurements")
+    ap.add_argument("--glass", action="store_true",
+                    help="also run the perturbed-glass stand-in sweeps (off by default)")
     ap.add_argument("--profile", action="store_true",
                     help="build once and run the walk twice on --sink-sample sinks (for ncu)")
     ap.add_argument("--sink-sample", type=int, default=1 << 20)

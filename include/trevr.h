@@ -75,7 +75,7 @@ typedef struct {
                            centre of luminosity is moved radially onto that sphere before
                            its ray is traced (the ray then ends in the leaf holding the
                            moved point). 0 = off. Only trevr_compute_flux accepts it. */
-    float tau_stop;     /* > 0: early ray termination (Sec. 5, proposed there): a ray's
+    float tau_stop;     /* > 0: early ray termination (Sec. 4, proposed there): a ray's
                            optical depth sum stops once it exceeds tau_stop, and the ray
                            then adds nothing (the flux drops by at most exp(-tau_stop)
                            times its unabsorbed value). The fp32 running sum decides.
@@ -156,7 +156,7 @@ int trevr_compute_flux(const trevr_tree* t, const long long* sink_idx, long long
                        trevr_stats* stats, void* stream);
 
 /*
- * Several bands (Sec. 5: many bands of radiation for a constant factor in cost).
+ * Several bands (Sec. 4: many bands of radiation for a constant factor in cost).
  * Band b has its own absorption coefficient per particle and its own
  * luminosity per source. The bands share the walk and the rays. The tree, the
  * centres of luminosity and the opening-angle test use the band-summed
@@ -340,6 +340,8 @@ void trevr_tree_free(trevr_tree* t);
  * (cudaGetSymbolAddress) with that device current; make that first call before
  * any stream capture. Every call shares the one array and overwrites it, so
  * calls whose work overlaps on the GPU (other streams or host threads) race.
+ * The looked-up address is kept for the life of the process: after a
+ * cudaDeviceReset of a device, do not call this function on that device again.
  * A point outside the domain returns TREVR_ERR_OUT_OF_DOMAIN.
  */
 #define TREVR_NOALLOC_MAX_N (1 << 20)

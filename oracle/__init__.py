@@ -311,7 +311,7 @@ class OracleTree:
 
     def flux_terminated(self, theta, tau_ref, tau_stop, sinks=None, nthreads=0,
                         with_counters=False, bg_radius=0.0):
-        """Flux with early ray termination (Sec. 5): a ray whose optical depth passes
+        """Flux with early ray termination (Sec. 4): a ray whose optical depth passes
         tau_stop > 0 adds nothing (bg_radius > 0: with the background sources of
         flux_background). counters columns: interactions, segments, visited source nodes,
         refinements (of the complete rays), terminated rays."""

@@ -525,7 +525,7 @@ nomem:
 }
 
 /*
- * Several bands (Sec. 5: many bands for a constant factor in cost). Band b has its
+ * Several bands (Sec. 4: many bands for a constant factor in cost). Band b has its
  * own absorption alpha_b (band-major, n_bands x n_gas) and its own source
  * luminosities L_b (n_bands x n_src). Reading: the walk and the rays are shared
  * by the bands. The tree, the centres of luminosity and the opening-angle test
@@ -986,7 +986,7 @@ typedef struct {
 /* Options of one walk beyond theta and tau_ref (all off when zero). */
 typedef struct {
     float bg_radius;  /* > 0: background sources on this sphere (Sec. 2.2.4) */
-    float tau_stop;   /* > 0: early ray termination (Sec. 5) */
+    float tau_stop;   /* > 0: early ray termination (Sec. 4) */
     int sub_bucket;   /* particle trace below the buckets (Sec. 2.2.3, 3.1.3) */
     nsum_t *bandF;    /* per-band flux accumulators (trees with bands) */
 } walkopt_t;
@@ -994,7 +994,7 @@ typedef struct {
 static const walkopt_t NO_OPTS = {0.0f, 0.0f, 0, NULL};
 
 /* One pseudo-source (L at q, inside node C) seen from sorted particle i.
-   tau_stop > 0: early ray termination (Sec. 5, proposed there). The optical depth
+   tau_stop > 0: early ray termination (Sec. 4, proposed there). The optical depth
    sum of a ray is abandoned once it passes tau_stop, and the ray then adds nothing.
    Every term of the sum is non-negative, so a partial sum passes tau_stop exactly
    when the complete sum does: here the complete sum decides.
@@ -1279,7 +1279,7 @@ int orc_flux_background(const orc_tree *T, const int64_t *sinks, int64_t n_sink,
     return ORC_OK;
 }
 
-/* Flux with early ray termination at optical depth tau_stop > 0 (Sec. 5), and
+/* Flux with early ray termination at optical depth tau_stop > 0 (Sec. 4), and
    with background sources on the sphere of radius bg_radius when it is > 0.
    counters (nullable) gets 5 int64 per sink: interactions, segments, visited
    source nodes, refinements and terminated rays (segments and refinements

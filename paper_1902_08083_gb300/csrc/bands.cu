@@ -1,4 +1,4 @@
-// Trees with several bands (Sec. 5: many bands for a constant factor in cost).
+// Trees with several bands (Sec. 4: many bands for a constant factor in cost).
 //
 // Band b has its own absorption alpha_b per particle and luminosity L_b per source.
 // The bands share the walk and the rays. The tree is built as a single-band tree

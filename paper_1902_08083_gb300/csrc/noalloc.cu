@@ -44,6 +44,9 @@ unsigned char* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device; looked up once per
 // device (the host-side name of a __device__ array is not a device address).
+// The cached address belongs to the device's current context: after
+// cudaDeviceReset the module is loaded again and the array may move, so a
+// process that resets a device must not call this entry point on it again.
 cudaError_t scratch_on_current_device(unsigned char** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -106,7 +109,8 @@ extern "C" int trevr_morton_sort_noalloc(const float* gas_xyz, long long n_gas,
   int* status = reinterpret_cast<int*>(base + kOffStatus);
   // the status word must start at zero; the rest of the scratch is fully
   // overwritten before it is read
-  cudaMemsetAsync(status, 0, sizeof(int), s);
+  err = cudaMemsetAsync(status, 0, sizeof(int), s);
+  if (err != cudaSuccess) return cuda_to_error(err);
   Domain32 D;
   for (int d = 0; d < 3; ++d) {
     volatile float lo = dom->lo[d], side = dom->side;
@@ -124,8 +128,8 @@ extern "C" int trevr_morton_sort_noalloc(const float* gas_xyz, long long n_gas,
   note_launch();
   radix_sort(keys_out, reinterpret_cast<unsigned*>(perm_out), n, 63, S, s);
   int h_status = 0;
-  cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s);
-  err = cudaStreamSynchronize(s);
+  err = cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
   if (err == cudaSuccess) err = cudaGetLastError();
   if (err != cudaSuccess) return cuda_to_error(err);
   return status_to_error(h_status);

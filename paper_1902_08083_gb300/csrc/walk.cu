@@ -723,7 +723,7 @@ __device__ __forceinline__ float sub_bucket_tau_warp(const TreeView& T, int src,
 
 // Rays from the sinks of the lanes in `on` to (q, L) inside cell C; every lane
 // of the warp must call it (the loop runs while any lane has cells left).
-// STOP: early ray termination (Sec. 5): a lane whose running optical depth passes
+// STOP: early ray termination (Sec. 4): a lane whose running optical depth passes
 // P.tau_stop drops the rest of its ray, and the ray adds nothing.
 // NB > 1: several bands (2 or 4 slots of the band records): every band sums its own
 // optical depth over the shared segments, and F[b] gets band b's flux.

@@ -186,12 +186,14 @@ class Tree:
             if alpha.shape[1] != self.n_gas or (self.n_src and
                                                 tuple(src_lum.shape) != (self.n_bands, self.n_src)):
                 raise ValueError("alpha (B, N) and src_lum (B, S) must have the same B")
+            alpha_c = alpha.contiguous()  # kept alive until the call has returned
+            lum_c = src_lum.contiguous() if self.n_src else None
             rc = lib.trevr_build_tree_bands(
                 _dev_ptr(gas_xyz, torch.float32, "gas_xyz"),
-                _dev_ptr(alpha.contiguous(), torch.float32, "alpha"),
+                _dev_ptr(alpha_c, torch.float32, "alpha"),
                 _dev_ptr(weight, torch.float32, "weight"), self.n_gas,
                 _dev_ptr(src_xyz, torch.float32, "src_xyz") if self.n_src else None,
-                _dev_ptr(src_lum.contiguous(), torch.float32, "src_lum") if self.n_src else None,
+                _dev_ptr(lum_c, torch.float32, "src_lum") if self.n_src else None,
                 self.n_src, self.n_bands, ctypes.byref(dom), ctypes.byref(prm),
                 _stream_ptr(stream), ctypes.byref(h))
             where = "trevr_build_tree_bands"
@@ -333,19 +335,44 @@ def compute_flux_bands(tree: Tree, theta=0.75, tau_ref=0.1, sink_idx=None, out=N
 def morton_sort_noalloc(gas_xyz, lo=(0.0, 0.0, 0.0), side=1.0, keys_out=None, perm_out=None,
                         stream=None):
     """Morton keys and stable sort of the particles (trevr_morton_sort_noalloc): the
-    library allocates nothing; the output tensors are allocated here unless given."""
-    lib = load_library()
+    library allocates nothing; the output tensors are allocated here unless given.
+
+    gas_xyz is (3, N) fp32; keys_out (int64) and perm_out (int32) must hold at least
+    N elements. Every tensor must sit on one CUDA device, which is made current for
+    the call (the C side looks up its scratch array on the current device and
+    launches there); `stream`, if given, must belong to that device."""
+    # shapes, sizes and devices first (no GPU needed to reject them), then CUDA
+    if not isinstance(gas_xyz, torch.Tensor):
+        raise TypeError("gas_xyz must be a CUDA tensor")
+    if gas_xyz.dim() != 2 or gas_xyz.shape[0] != 3:
+        raise ValueError(f"gas_xyz must have shape (3, N), got {tuple(gas_xyz.shape)}")
+    dev = gas_xyz.device
     n = int(gas_xyz.shape[1])
-    if keys_out is None:
-        keys_out = torch.empty(n, dtype=torch.int64, device=gas_xyz.device)
-    if perm_out is None:
-        perm_out = torch.empty(n, dtype=torch.int32, device=gas_xyz.device)
-    dom = Domain((ctypes.c_float * 3)(*[float(v) for v in lo]), float(side))
-    rc = lib.trevr_morton_sort_noalloc(_dev_ptr(gas_xyz.contiguous(), torch.float32, "gas_xyz"),
-                                       n, ctypes.byref(dom),
-                                       _dev_ptr(keys_out, torch.int64, "keys_out"),
-                                       _dev_ptr(perm_out, torch.int32, "perm_out"),
-                                       _stream_ptr(stream))
+    for name, t in (("keys_out", keys_out), ("perm_out", perm_out)):
+        if t is None:
+            continue
+        if not isinstance(t, torch.Tensor) or t.device != dev:
+            raise ValueError(f"{name} must be a tensor on {dev}")
+        if t.numel() < n:
+            raise ValueError(f"{name} holds {t.numel()} elements, fewer than the {n} particles")
+    if stream is not None and stream.device != dev:
+        raise ValueError(f"stream belongs to {stream.device}, the tensors to {dev}")
+    if not gas_xyz.is_cuda:
+        raise TypeError("gas_xyz must be a CUDA tensor")
+    lib = load_library()
+    with torch.cuda.device(dev):
+        if keys_out is None:
+            keys_out = torch.empty(n, dtype=torch.int64, device=dev)
+        if perm_out is None:
+            perm_out = torch.empty(n, dtype=torch.int32, device=dev)
+        xyz = gas_xyz.contiguous()  # kept alive until the call has returned
+        dom = Domain((ctypes.c_float * 3)(*[float(v) for v in lo]), float(side))
+        rc = lib.trevr_morton_sort_noalloc(_dev_ptr(xyz, torch.float32, "gas_xyz"),
+                                           n, ctypes.byref(dom),
+                                           _dev_ptr(keys_out, torch.int64, "keys_out"),
+                                           _dev_ptr(perm_out, torch.int32, "perm_out"),
+                                           _stream_ptr(stream))
+        del xyz
     if rc != TREVR_OK:
         raise TrevrError(rc, "trevr_morton_sort_noalloc")
     return keys_out, perm_out

@@ -1,4 +1,4 @@
-"""Several bands on the GPU (Sec. 5): the bands share the walk and the rays, each
+"""Several bands on the GPU (Sec. 4): the bands share the walk and the rays, each
 band sums its own optical depth, and a cell refines when any band asks. GPU vs the
 oracle's band flux per band, with the counters of the shared walk; one band equal
 to the plain flux; proportional bands equal to scaled copies of the plain flux."""

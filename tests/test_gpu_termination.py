@@ -1,4 +1,4 @@
-"""Early ray termination on the GPU (Sec. 5): the running optical depth of a ray is
+"""Early ray termination on the GPU (Sec. 4): the running optical depth of a ray is
 compared with tau_stop after each segment, and a ray that passes it adds nothing.
 
 The kernel decides on its fp32 running sum, the oracle on the FP64 total. The two can

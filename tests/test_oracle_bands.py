@@ -1,4 +1,4 @@
-"""Several bands (Sec. 5: many bands for a constant factor in cost). Reading: the
+"""Several bands (Sec. 4: many bands for a constant factor in cost). Reading: the
 bands share the walk and the rays. The tree's centres of luminosity come from the
 band-summed luminosity. A cell is refined when any band asks for it, and each band
 sums its own optical depth along the shared segments.

@@ -1,4 +1,4 @@
-"""Early ray termination (Sec. 5, proposed there): a ray whose optical depth sum
+"""Early ray termination (Sec. 4, proposed there): a ray whose optical depth sum
 passes tau_stop is abandoned and adds nothing.
 
 Pins: the closed form for one source in a uniform medium (every ray's optical depth
