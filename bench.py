@@ -148,11 +148,13 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
-def _walk_traffic_per_sink():
-    """DRAM bytes per sink of the walk kernel from the last ncu capture, scaled by the
-    sinks of a launch; None if the kernel source changed since that capture."""
+def _kernel_profile(name):
+    """Per-sink counters of one kernel from a committed ncu capture
+    (profiles/<name>): warp instructions issued, thread instructions executed, DRAM
+    bytes, and the cell steps of the captured sinks. None if the kernel's source has
+    changed since the capture (the counters would describe another kernel)."""
     import hashlib
-    p = os.path.join(ROOT, "profiles", "walk_warp_kernel_dram.json")
+    p = os.path.join(ROOT, "profiles", name)
     try:
         d = json.load(open(p))
         src = open(os.path.join(ROOT, d["source"]), "rb").read()
@@ -160,7 +162,48 @@ def _walk_traffic_per_sink():
         return None
     if hashlib.sha256(src).hexdigest() != d["source_sha256"]:
         return None
-    return float(d["dram_bytes_per_sink"])
+    d["file"] = name
+    return d
+
+
+def _issue_roofline(prof, sinks, t_s, sm_mhz, n_sm, alg_bytes, peak_gbs, peak_kind, kernel):
+    """Roofline of an issue-bound walk. achieved = warp instructions issued per launch
+    (the capture's per-sink count times the launch's sinks) over the event-timed
+    launch; peak = 4 schedulers x n_sm SMs x 1 warp instruction per cycle at the SM
+    clock sampled during the timed region. The logical bytes of cell records per
+    second stay beside it as a secondary figure against the HBM copy bandwidth."""
+    logical = {"achieved": alg_bytes / t_s / 1e9, "peak": peak_gbs, "unit": "GB/s",
+               "frac": alg_bytes / t_s / 1e9 / peak_gbs, "bytes_per_launch": alg_bytes,
+               "peak_kind": f"{peak_kind} (copy bandwidth)",
+               "note": "logical cell-record reads, mostly L1/L2 hits"}
+    peak = 4 * n_sm * sm_mhz * 1e6 / 1e9
+    if prof is None:
+        return {"bound": "issue", "achieved": None, "peak": peak,
+                "unit": "G warp-instructions/s", "frac": None, "traffic": None,
+                "kernel": kernel, "stale": "kernel source changed since the ncu capture",
+                "logical_bytes": logical}
+    per_sink = prof["warp_inst_issued"] / prof["sinks"]
+    achieved = per_sink * sinks / t_s / 1e9
+    steps = prof["cells_tested"] + prof["cells_clipped"]
+    return {"bound": "issue", "achieved": achieved, "peak": peak,
+            "unit": "G warp-instructions/s", "frac": achieved / peak,
+            "traffic": prof["dram_bytes_per_sink"] * sinks, "kernel": kernel,
+            "peak_kind": f"issue limit: 4 schedulers x {n_sm} SMs x 1 warp-instruction/cycle "
+                         f"at {sm_mhz:.0f} MHz (SM clock sampled under load)",
+            "instructions_per_launch": per_sink * sinks,
+            "thread_instructions_per_cell_step": prof["thread_inst_executed"] / steps,
+            "active_lanes_per_instruction": prof["thread_inst_executed"] /
+                                            prof["warp_inst_issued"],
+            "counters_from": f"profiles/{prof['file']} ({prof['sinks']} sinks, ncu)",
+            "logical_bytes": logical}
+
+
+def _peaks_clock():
+    """Maximum SM clock (MHz) from MEASURED_PEAKS.json, else the GB300's 2070 MHz."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p)).get("sm_max_mhz", 2070.0))
+    return 2070.0
 
 
 def _peaks():
@@ -274,7 +317,7 @@ def _time_ms(fn, reps, stream):
     return out
 
 
-def _bench_batched(args):
+def _bench_batched(args, sm_mhz):
     """64 independent boxes (2^12..2^17 particles, log-uniform): one persistent launch
     replayed from a CUDA graph, launch shape from the autotuner, vs 64 plain calls."""
     import torch
@@ -293,6 +336,7 @@ def _bench_batched(args):
     tune = autotune.tune(B, th, tr)
     shape = dict(sinks_per_warp=tune["sinks_per_warp"], block_size=tune["block_size"],
                  walk_variant=tune.get("walk_variant", 0))
+    st = B.run(th, tr, stats=True, **shape)  # counters (untimed) for the roofline
     B.capture(th, tr, **shape)
     for _ in range(args.warmup):
         B.replay()
@@ -306,11 +350,24 @@ def _bench_batched(args):
     t_seq = _time_ms(sequential, args.steps, stream)
     same = all(torch.equal(a, b) for a, b in zip(B.flux, outs))
     n = B.n_sinks
+    t_rep = sum(t_graph) / len(t_graph) * 1e-3
+    alg_bytes = 20 * n + 32 * st["src_nodes_visited"] + 32 * st["cells_clipped"]
+    peak, peak_kind = _peaks()
+    dev_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    prof = _kernel_profile("walk_warp_batched_kernel_issue.json")
+    if prof is not None and prof.get("launch_shape") != shape:
+        prof = None  # the capture was of another launch shape
     res = {"workload": f"{len(trees)} boxes, {n} sinks (2^12..2^17 each), theta 0.75, tau_ref 0.1",
            "graph_fluxes_per_s": n / (min(t_graph) * 1e-3),
            "sequential_fluxes_per_s": n / (min(t_seq) * 1e-3),
            "speedup": min(t_seq) / min(t_graph), "bit_equal_to_sequential": bool(same),
-           "launch_shape": shape, "tuned_from_cache": bool(tune.get("cached"))}
+           "launch_shape": shape, "tuned_from_cache": bool(tune.get("cached")),
+           "per_sink": {"interactions": st["interactions"] / n, "segments": st["segments"] / n,
+                        "cells_visited": st["src_nodes_visited"] / n,
+                        "cells_clipped": st["cells_clipped"] / n},
+           "roofline": _issue_roofline(prof, n, t_rep, sm_mhz, dev_sm, alg_bytes, peak,
+                                       peak_kind, "walk_warp_batched_kernel (persistent, "
+                                       "graph replay)")}
     B.free()
     for t in trees:
         t.free()
@@ -584,19 +641,21 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return
 
-    # roofline of the dominant kernel (the sink walk): algorithmic bytes per launch =
+    # roofline of the dominant kernel (the sink walk). Its cell records are L1/L2 hits
+    # (DRAM carries ~80 B per sink), and it is bound by instruction issue: achieved =
+    # warp instructions issued per launch / the walk's event-timed duration, against
+    # the issue limit of the SMs at the sampled clock. Secondary: the logical bytes,
     # 20 B per sink (position, leaf, flux) + 32 B per source cell tested + 32 B per
-    # cell clipped by a ray, divided by the walk's event-timed duration
+    # cell clipped by a ray, per second against the HBM copy bandwidth.
     alg_bytes = 20 * n + 32 * st["src_nodes_visited"] + 32 * st["cells_clipped"]
-    traffic = _walk_traffic_per_sink()
-    traffic = None if traffic is None else traffic * n
     t_walk = sum(walk_ms) / len(walk_ms) * 1e-3
     peak, peak_kind = _peaks()
-    achieved = alg_bytes / t_walk / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "walk_warp_kernel, variant 3 (warp-shared walk, merged rays, flux)",
-                "peak_kind": f"{peak_kind} (copy bandwidth, burst)",
-                "bytes_per_launch": alg_bytes}
+    sm_mhz = clk.get("sm_mhz") or _peaks_clock()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    roofline = _issue_roofline(_kernel_profile("walk_warp_kernel_issue.json"), n, t_walk,
+                               sm_mhz, n_sm, alg_bytes, peak, peak_kind,
+                               "walk_warp_kernel, variant 3 (warp-shared walk, merged rays, "
+                               "flux, no counters)")
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
@@ -615,7 +674,7 @@ def run_ours(args):
             "gpu_launches": int(launches), "clocks": clk}
 
     if world == 1 and not args.no_extras:
-        line["batched"] = _bench_batched(args)
+        line["batched"] = _bench_batched(args, sm_mhz)
         line["adjoint"] = _bench_adjoint(args)
         line["terminated"] = _bench_termination(args, P, g)
         line["bands"] = _bench_bands(args, P, g)
@@ -639,8 +698,10 @@ def run_ours(args):
 
 
 def run_profile(args):
-    """A short program for ncu: one tree build, then the walk twice on a contiguous
-    Morton-ordered run of sinks (the second launch is the one to capture)."""
+    """A short program for ncu: one tree build, then on a contiguous Morton-ordered run
+    of --sink-sample sinks the walk with counters (launch 0, whose counters are
+    printed) and the walk the benchmark times, without counters (launch 1, the one
+    to capture: -k regex:walk_warp_kernel -s 1 -c 1)."""
     import torch
     from paper_1902_08083_gb300 import trevr
     torch.cuda.set_device(0)
@@ -656,12 +717,45 @@ def run_profile(args):
     perm = tree.export()["perm"]
     start = (n - m) // 2
     sinks = perm[start:start + m].to(torch.int64).contiguous()
-    for _ in range(2):
-        f = trevr.compute_flux(tree, P["theta"], P["tau_ref"], sink_idx=sinks)
+    _, st = trevr.compute_flux(tree, P["theta"], P["tau_ref"], sink_idx=sinks, stats=True)
+    f = trevr.compute_flux(tree, P["theta"], P["tau_ref"], sink_idx=sinks)
     torch.cuda.synchronize()
     print(json.dumps({"profile": args.workload, "n_gas": n, "sinks": m,
+                      "cells_tested": st["src_nodes_visited"],
+                      "cells_clipped": st["cells_clipped"],
                       "flux_sum": float(f.double().sum())}), flush=True)
     tree.free()
+
+
+def run_profile_batched(args):
+    """A short program for ncu on the batched walk: the 64 boxes, the autotuned launch
+    shape, one batched call with counters (launch 0, counters printed) and one without
+    (launch 1, the one to capture: -k regex:walk_warp_batched_kernel -s 1 -c 1)."""
+    import torch
+    from paper_1902_08083_gb300 import autotune, trevr
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    boxes = workloads.batched_boxes()
+    trees = []
+    for P in boxes:
+        g = {k: torch.from_numpy(np.ascontiguousarray(P[k])).to(dev)
+             for k in ("gas_xyz", "alpha", "src_xyz", "src_lum")}
+        trees.append(trevr.build_tree(g["gas_xyz"], g["alpha"], g["src_xyz"], g["src_lum"],
+                                      lo=P["lo"], side=P["side"], bucket=P["bucket"]))
+    th, tr = boxes[0]["theta"], boxes[0]["tau_ref"]
+    B = trevr.Batch(trees)
+    tune = autotune.tune(B, th, tr)
+    shape = dict(sinks_per_warp=tune["sinks_per_warp"], block_size=tune["block_size"],
+                 walk_variant=tune.get("walk_variant", 0))
+    st = B.run(th, tr, stats=True, **shape)
+    B.run(th, tr, **shape)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "batched", "sinks": B.n_sinks, "launch_shape": shape,
+                      "cells_tested": st["src_nodes_visited"],
+                      "cells_clipped": st["cells_clipped"]}), flush=True)
+    B.free()
+    for t in trees:
+        t.free()
 
 
 def main():
@@ -685,12 +779,16 @@ def main():
                     help="also run the perturbed-glass stand-in sweeps (off by default)")
     ap.add_argument("--profile", action="store_true",
                     help="build once and run the walk twice on --sink-sample sinks (for ncu)")
+    ap.add_argument("--profile-batched", action="store_true",
+                    help="the 64 boxes: one batched walk with counters, one without (for ncu)")
     ap.add_argument("--sink-sample", type=int, default=1 << 20)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.profile:
         run_profile(args)
+    elif args.profile_batched:
+        run_profile_batched(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

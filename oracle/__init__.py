@@ -100,6 +100,11 @@ def _load():
         lib.orc_replay_free.restype = None
         lib.orc_replay_loss.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_double]
         lib.orc_replay_loss.restype = ctypes.c_double
+        lib.orc_replay_loss_planes.argtypes = [P, P, P, ctypes.c_int, i64, ctypes.c_double,
+                                               ctypes.c_int]
+        lib.orc_replay_loss_planes.restype = ctypes.c_double
+        lib.orc_replay_kinks.argtypes = [P, P, ctypes.c_int, i64, ctypes.c_double]
+        lib.orc_replay_kinks.restype = i64
         lib.orc_leaf_of_point.argtypes = [P, f32, f32, f32]
         lib.orc_leaf_of_point.restype = i64
         _lib = lib
@@ -411,8 +416,18 @@ class Replay:
             self.tree._lib.orc_replay_free(self._h)
             self._h = None
 
-    def loss(self, w, kind=-1, index=0, h=0.0):
+    def loss(self, w, kind=-1, index=0, h=0.0, frozen_planes=False):
+        """frozen_planes: every segment keeps the bounding slab planes of the
+        unperturbed ray, which makes the loss analytic in h (the function the
+        adjoint differentiates); otherwise lengths are re-clipped (kinks where a
+        bounding plane switches)."""
         w = np.ascontiguousarray(w, dtype=np.float64)
         assert w.shape[0] == self.n_sink
-        return float(self.tree._lib.orc_replay_loss(self.tree._h, self._h, _ptr(w), int(kind),
-                                                    int(index), float(h)))
+        return float(self.tree._lib.orc_replay_loss_planes(self.tree._h, self._h, _ptr(w),
+                                                           int(kind), int(index), float(h),
+                                                           int(bool(frozen_planes))))
+
+    def kinks(self, kind, index, h):
+        """Recorded segments whose bounding planes differ between -h and +h."""
+        return int(self.tree._lib.orc_replay_kinks(self.tree._h, self._h, int(kind),
+                                                   int(index), float(h)))

@@ -1874,41 +1874,121 @@ static double seg_len64(const orc_tree *T, const double P[3], const double Q[3],
     return t1 > t0 ? (t1 - t0) * sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]) : 0.0;
 }
 
+/* Bounding planes of the segment p->q inside node X (FP64, as seg_len64): plane
+   2k+0 is the box's lower face on axis k, 2k+1 its upper face; *e0 is the plane
+   that sets the entry t0 and *e1 the one that sets the exit t1, -1 where the ray
+   starts or ends inside X (t clamped to 0 or 1). Returns 0 when the ray misses X. */
+static int seg_planes64(const orc_tree *T, const double P[3], const double Q[3], int64_t X,
+                        int *e0, int *e1)
+{
+    double D[3] = {Q[0] - P[0], Q[1] - P[1], Q[2] - P[2]};
+    double t0 = 0.0, t1 = 1.0;
+    *e0 = -1;
+    *e1 = -1;
+    for (int k = 0; k < 3; ++k) {
+        double lo = T->lo[k] + (double)T->glo[X][k] * T->h;
+        double hi = T->lo[k] + (double)T->ghi[X][k] * T->h;
+        if (D[k] != 0.0) {
+            double ta = (lo - P[k]) / D[k], tb = (hi - P[k]) / D[k];
+            int pa = 2 * k, pb = 2 * k + 1;
+            double tn = ta, tx = tb;
+            int pn = pa, px = pb;
+            if (tb < ta) {
+                tn = tb; tx = ta; pn = pb; px = pa;
+            }
+            if (tn > t0) { t0 = tn; *e0 = pn; }
+            if (tx < t1) { t1 = tx; *e1 = px; }
+        } else if (P[k] < lo || P[k] >= hi) {
+            return 0;
+        }
+    }
+    return t1 > t0;
+}
+
+/* FP64 length of the segment p->q inside X with its bounding planes given (as
+   seg_planes64 found them for another end point): (t1 - t0) |q - p| with t of
+   plane b on axis k equal to (b - p_k)/(q_k - p_k). An analytic function of q. */
+static double seg_len64_planes(const orc_tree *T, const double P[3], const double Q[3],
+                               int64_t X, int e0, int e1)
+{
+    double D[3] = {Q[0] - P[0], Q[1] - P[1], Q[2] - P[2]};
+    double t0 = 0.0, t1 = 1.0;
+    if (e0 >= 0) {
+        int k = e0 / 2;
+        double b = T->lo[k] + (double)(e0 % 2 ? T->ghi[X][k] : T->glo[X][k]) * T->h;
+        t0 = (b - P[k]) / D[k];
+    }
+    if (e1 >= 0) {
+        int k = e1 / 2;
+        double b = T->lo[k] + (double)(e1 % 2 ? T->ghi[X][k] : T->glo[X][k]) * T->h;
+        t1 = (b - P[k]) / D[k];
+    }
+    return (t1 - t0) * sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+}
+
+/* The perturbed moments of one replay evaluation: luminosity and centre of every
+   cell, the luminosity of the perturbed source, and the change of every cell's
+   mean absorption (kind 0: source `index` has L += h; kind 1: particle `index`
+   has alpha += h; kind -1: none). */
+typedef struct {
+    double *dabar, *Lp, (*cp)[3];
+    int64_t psrc;
+    double srcL;
+} replay_pert_t;
+
+static void replay_perturb(const orc_tree *T, int kind, int64_t index, double h, replay_pert_t *o)
+{
+    const int64_t nn = T->n_nodes;
+    o->dabar = calloc((size_t)nn, sizeof(double));
+    o->Lp = malloc((size_t)nn * sizeof(double));
+    o->cp = malloc((size_t)nn * sizeof(*o->cp));
+    for (int64_t X = 0; X < nn; ++X) {
+        o->Lp[X] = T->L[X];
+        for (int d = 0; d < 3; ++d) o->cp[X][d] = T->cen[X][d];
+    }
+    o->psrc = -1;
+    o->srcL = 0.0;
+    if (kind == 0) {
+        for (int64_t s = 0; s < T->n_src; ++s)
+            if (T->src_order[s] == index) o->psrc = s;
+        const int64_t ps = o->psrc;
+        const double y[3] = {(double)T->sx[ps], (double)T->sy[ps], (double)T->sz[ps]};
+        for (int64_t C = T->src_leaf[ps]; C >= 0; C = T->parent[C]) {
+            double Ln = T->L[C] + h;
+            for (int d = 0; d < 3; ++d) o->cp[C][d] = (T->L[C] * T->cen[C][d] + h * y[d]) / Ln;
+            o->Lp[C] = Ln;
+        }
+        o->srcL = (double)T->slum[ps] + h;
+    } else if (kind == 1) {
+        int64_t i = T->rank[index];
+        for (int64_t X = T->leaf_of[i]; X >= 0; X = T->parent[X])
+            o->dabar[X] = (double)T->w[i] * h / T->W[X];
+    }
+}
+
+static void replay_pert_free(replay_pert_t *o)
+{
+    free(o->dabar);
+    free(o->Lp);
+    free(o->cp);
+}
+
 /*
  * Loss sum_k w[k] log F_k over the recorded sinks, with one input perturbed:
  * kind 0: luminosity of source `index` (caller order) += h;
  * kind 1: alpha of particle `index` (caller order) += h;
  * kind -1: no perturbation.  Moments are updated exactly for the perturbation.
+ * frozen_planes = 0: each segment's length is the FP64 clip of the moved ray (the
+ * loss whose decisions are frozen; it has kinks where a bounding plane switches).
+ * frozen_planes = 1: each segment keeps the bounding planes of the unperturbed
+ * ray, so the loss is analytic in h; its derivative at h = 0 is the same, and it
+ * is the function the adjoint differentiates.
  */
-double orc_replay_loss(const orc_tree *T, const orc_replay *r, const double *w, int kind,
-                       int64_t index, double h)
+double orc_replay_loss_planes(const orc_tree *T, const orc_replay *r, const double *w, int kind,
+                              int64_t index, double h, int frozen_planes)
 {
-    /* perturbed quantities, as overrides of the affected nodes */
-    const int64_t nn = T->n_nodes;
-    double *dabar = calloc((size_t)nn, sizeof(double));
-    double *Lp = malloc((size_t)nn * sizeof(double));
-    double (*cp)[3] = malloc((size_t)nn * sizeof(*cp));
-    for (int64_t X = 0; X < nn; ++X) {
-        Lp[X] = T->L[X];
-        for (int d = 0; d < 3; ++d) cp[X][d] = T->cen[X][d];
-    }
-    int64_t psrc = -1;
-    double srcL = 0.0;
-    if (kind == 0) {
-        for (int64_t s = 0; s < T->n_src; ++s)
-            if (T->src_order[s] == index) psrc = s;
-        const double y[3] = {(double)T->sx[psrc], (double)T->sy[psrc], (double)T->sz[psrc]};
-        for (int64_t C = T->src_leaf[psrc]; C >= 0; C = T->parent[C]) {
-            double Ln = T->L[C] + h;
-            for (int d = 0; d < 3; ++d) cp[C][d] = (T->L[C] * T->cen[C][d] + h * y[d]) / Ln;
-            Lp[C] = Ln;
-        }
-        srcL = (double)T->slum[psrc] + h;
-    } else if (kind == 1) {
-        int64_t i = T->rank[index];
-        for (int64_t X = T->leaf_of[i]; X >= 0; X = T->parent[X])
-            dabar[X] = (double)T->w[i] * h / T->W[X];
-    }
+    replay_pert_t pt;
+    replay_perturb(T, kind, index, h, &pt);
     double loss = 0.0;
 #ifdef _OPENMP
 #pragma omp parallel for reduction(+ : loss) schedule(dynamic, 16)
@@ -1919,20 +1999,29 @@ double orc_replay_loss(const orc_tree *T, const orc_replay *r, const double *w, 
         nsum_t F = {0.0, 0.0};
         for (int64_t q = r->ia_start[k]; q < r->ia_start[k + 1]; ++q) {
             int64_t C = r->ia_node[q], s = r->ia_src[q];
-            double Q[3], L;
+            double Q[3], Q0[3], L;
             if (s >= 0) {
                 Q[0] = (double)T->sx[s];
                 Q[1] = (double)T->sy[s];
                 Q[2] = (double)T->sz[s];
-                L = (s == psrc) ? srcL : (double)T->slum[s];
+                L = (s == pt.psrc) ? pt.srcL : (double)T->slum[s];
             } else {
-                for (int d = 0; d < 3; ++d) Q[d] = cp[C][d];
-                L = Lp[C];
+                for (int d = 0; d < 3; ++d) Q[d] = pt.cp[C][d];
+                L = pt.Lp[C];
             }
+            for (int d = 0; d < 3; ++d) Q0[d] = s >= 0 ? Q[d] : T->cen[C][d];
             nsum_t tau = {0.0, 0.0};
             for (int64_t g = r->ia_seg0[q]; g < r->ia_seg0[q + 1]; ++g) {
                 int64_t X = r->seg_box[g];
-                nsum_add(&tau, (T->abar[X] + dabar[X]) * seg_len64(T, P, Q, X));
+                double l;
+                if (frozen_planes) {
+                    int e0, e1;
+                    l = seg_planes64(T, P, Q0, X, &e0, &e1) ?
+                        seg_len64_planes(T, P, Q, X, e0, e1) : 0.0;
+                } else {
+                    l = seg_len64(T, P, Q, X);
+                }
+                nsum_add(&tau, (T->abar[X] + pt.dabar[X]) * l);
             }
             double s2 = 0.0;
             for (int d = 0; d < 3; ++d) s2 += (Q[d] - P[d]) * (Q[d] - P[d]);
@@ -1940,8 +2029,50 @@ double orc_replay_loss(const orc_tree *T, const orc_replay *r, const double *w, 
         }
         loss += w[k] * log(nsum_get(&F));
     }
-    free(dabar);
-    free(Lp);
-    free(cp);
+    replay_pert_free(&pt);
     return loss;
+}
+
+double orc_replay_loss(const orc_tree *T, const orc_replay *r, const double *w, int kind,
+                       int64_t index, double h)
+{
+    return orc_replay_loss_planes(T, r, w, kind, index, h, 0);
+}
+
+/*
+ * Number of recorded segments whose bounding planes (seg_planes64) differ between
+ * the perturbations -h and +h of input `index` (kind as orc_replay_loss): each is a
+ * kink of the frozen-decision loss inside the central-difference step. Only a
+ * luminosity moves a ray (through the centres of luminosity), so kind 1 gives 0.
+ */
+int64_t orc_replay_kinks(const orc_tree *T, const orc_replay *r, int kind, int64_t index,
+                         double h)
+{
+    if (kind != 0) return 0;
+    replay_pert_t pm, pp;
+    replay_perturb(T, kind, index, -h, &pm);
+    replay_perturb(T, kind, index, h, &pp);
+    int64_t kinks = 0;
+#ifdef _OPENMP
+#pragma omp parallel for reduction(+ : kinks) schedule(dynamic, 16)
+#endif
+    for (int64_t k = 0; k < r->n_sink; ++k) {
+        int64_t i = r->sink_i[k];
+        const double P[3] = {(double)T->px[i], (double)T->py[i], (double)T->pz[i]};
+        for (int64_t q = r->ia_start[k]; q < r->ia_start[k + 1]; ++q) {
+            int64_t C = r->ia_node[q];
+            if (r->ia_src[q] >= 0) continue; /* a single source does not move */
+            const double *Qm = pm.cp[C], *Qp = pp.cp[C];
+            if (Qm[0] == Qp[0] && Qm[1] == Qp[1] && Qm[2] == Qp[2]) continue;
+            for (int64_t g = r->ia_seg0[q]; g < r->ia_seg0[q + 1]; ++g) {
+                int a0, a1, b0, b1;
+                int hm = seg_planes64(T, P, Qm, r->seg_box[g], &a0, &a1);
+                int hp = seg_planes64(T, P, Qp, r->seg_box[g], &b0, &b1);
+                if (hm != hp || (hm && (a0 != b0 || a1 != b1))) ++kinks;
+            }
+        }
+    }
+    replay_pert_free(&pm);
+    replay_pert_free(&pp);
+    return kinks;
 }

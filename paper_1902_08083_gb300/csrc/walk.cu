@@ -64,13 +64,18 @@ struct CSum {
   __device__ __forceinline__ float get() const { return __fadd_rn(s, c); }
 };
 
-// Plain fp32 running sum, for the optical depth of one ray in the warp walk: at
-// most a few dozen positive terms, so its relative error stays near 1e-6 and the
-// flux moves by about tau * 1e-6 (measured: 6e-7 at most on the clumpy workload,
-// for 3 % less walk time than the compensated sum).
-struct PSum {
-  float s = 0.0f;
-  __device__ __forceinline__ void add(float x) { s = __fadd_rn(s, x); }
+// Kahan-compensated fp32 running sum (branch-free), for the optical depth of one
+// ray in the warp walks: c carries the low-order part that each addition loses,
+// so the error of the sum stays within about 2 ulp of the total however many
+// terms a refined ray has.
+struct KSum {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
   __device__ __forceinline__ float get() const { return s; }
 };
 
@@ -771,8 +776,8 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
     }
   }
   const bool traced = active;
-  PSum tau;
-  PSum taub[NB];  // (NB > 1) optical depth of each band
+  KSum tau;
+  KSum taub[NB];  // (NB > 1) optical depth of each band
   bool cut = false;
   int b = 0, rsp = 0, boxes = 0, pass = 1;
   int slot = -1;  // the upper child of the pair popped last: clipped next
@@ -912,11 +917,11 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
               } else {
                 if (NB > 1) {
                   const float4 ab = __ldg(&T.bA[box]);
-                  taub[0].add(ab.x * l);
-                  taub[1].add(ab.y * l);
+                  taub[0].add(__fmul_rn(ab.x, l));
+                  taub[1].add(__fmul_rn(ab.y, l));
                   if (NB > 2) {
-                    taub[NB > 2 ? 2 : 0].add(ab.z * l);
-                    taub[NB > 2 ? 3 : 0].add(ab.w * l);
+                    taub[NB > 2 ? 2 : 0].add(__fmul_rn(ab.z, l));
+                    taub[NB > 2 ? 3 : 0].add(__fmul_rn(ab.w, l));
                   }
                 } else if (SUB && (P.tau_ref <= 0.0f ||
                                    __fmul_rn(__ldg(&T.dbk[box]), l) > P.tau_ref)) {
@@ -928,7 +933,7 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
                   sub_t1 = t1;
                   if (CNT) ++cnt.sub;
                 } else {
-                  tau.add(a.w * l);
+                  tau.add(__fmul_rn(a.w, l));
                 }
                 if (!ADJ && STOP && tau.get() > P.tau_stop) {
                   cut = true;  // the rest of the ray is not traced

@@ -52,18 +52,32 @@ def test_backward_matches_oracle_adjoint(theta, tau_ref, weighted, variant):
     assert np.median(rel[nz]) <= 1e-4
 
 
-def _fd_ok(R, w, kind, idx, val, ref, floor, tol=1e-3):
-    """Central differences of the frozen loss agree with ref to tol. The frozen loss
-    is piecewise smooth: a ray's length in a cell has a kink wherever the slab plane
-    that bounds it changes, and a luminosity moves the centroids of every cell that
-    holds its source, hence thousands of rays. Steps of 1e-3 relative can straddle
-    such kinks, so the step is reduced down to 1e-6 until one agrees."""
-    for r in (1e-3, 1e-4, 1e-5, 1e-6):
-        h = r * val
-        fd = (R.loss(w, kind, idx, h) - R.loss(w, kind, idx, -h)) / (2 * h)
+def _fd_check(R, w, kind, idx, val, ref, floor, tol=1e-3):
+    """Central differences (step 1e-3 relative, as in the configuration) against ref.
+
+    (1) The replay with every segment's bounding slab planes frozen as well is
+        analytic in the step, and it is the function the adjoint differentiates:
+        its difference at h = 1e-3 must agree, with no smaller step.
+    (2) The frozen-decision loss itself re-clips the moved rays, so it has a kink
+        wherever a bounding plane switches. Its difference at h = 1e-3 is reported;
+        where it disagrees, the replay must count plane switches inside that step,
+        and a smaller step (down to 1e-6) must agree.
+    Returns (frozen-plane agreement, plain agreement at 1e-3, explained)."""
+    h = 1e-3 * val
+    fdp = (R.loss(w, kind, idx, h, frozen_planes=True) -
+           R.loss(w, kind, idx, -h, frozen_planes=True)) / (2 * h)
+    planes_ok = abs(fdp - ref) <= tol * abs(ref) + floor
+    fd = (R.loss(w, kind, idx, h) - R.loss(w, kind, idx, -h)) / (2 * h)
+    if abs(fd - ref) <= tol * abs(ref) + floor:
+        return planes_ok, True, True
+    if R.kinks(kind, idx, h) == 0:
+        return planes_ok, False, False
+    for r in (1e-4, 1e-5, 1e-6):
+        hh = r * val
+        fd = (R.loss(w, kind, idx, hh) - R.loss(w, kind, idx, -hh)) / (2 * hh)
         if abs(fd - ref) <= tol * abs(ref) + floor:
-            return True
-    return False
+            return planes_ok, False, True
+    return planes_ok, False, False
 
 
 def test_autograd_full_size_fd_and_oracle():
@@ -96,15 +110,23 @@ def test_autograd_full_size_fd_and_oracle():
     ok, rel = _close(ga, ga_o)
     assert ok.all(), f"alpha grads vs FP64 adjoint: {np.count_nonzero(~ok)} off"
     R = T.replay(P["theta"], P["tau_ref"], sinks=sub)
-    bad = []
     fl, fa = 1e-6 * np.abs(gl_o).max(), 1e-6 * np.abs(ga_o).max()
-    for j in P["fd_src"]:
-        if not _fd_ok(R, wv, 0, int(j), float(P["src_lum"][j]), gl[j], fl):
-            bad.append(("L", int(j)))
+    coords = [(0, int(j), float(P["src_lum"][j]), gl[j], fl) for j in P["fd_src"]]
     # absorption coordinates: particles on the sampled sinks' rays have nonzero gradients
     rng = np.random.default_rng(6)
     cand = np.nonzero(np.abs(ga_o) > 1e-6 * np.abs(ga_o).max())[0]
-    for i in rng.choice(cand, 32, replace=False):
-        if not _fd_ok(R, wv, 1, int(i), float(P["alpha"][i]), ga[i], fa):
-            bad.append(("alpha", int(i)))
+    coords += [(1, int(i), float(P["alpha"][i]), ga[i], fa)
+               for i in rng.choice(cand, 32, replace=False)]
+    bad, plain_at_1e3 = [], {0: 0, 1: 0}
+    for kind, idx, val, ref, floor in coords:
+        planes_ok, plain_ok, explained = _fd_check(R, wv, kind, idx, val, ref, floor)
+        plain_at_1e3[kind] += plain_ok
+        if not (planes_ok and explained):
+            bad.append(("L" if kind == 0 else "alpha", idx, planes_ok, explained))
+    print(f"central differences at h = 1e-3 (frozen decisions, planes re-clipped): "
+          f"{plain_at_1e3[0]}/32 luminosities and {plain_at_1e3[1]}/32 absorption "
+          f"coefficients agree within 1e-3; with the planes frozen too: "
+          f"{64 - sum(1 for b in bad if not b[2])}/64")
     assert not bad, bad
+    # an absorption coefficient moves no ray, so its loss has no kinks at all
+    assert plain_at_1e3[1] == 32

@@ -102,8 +102,6 @@ def test_clumpy_full_size_sampled(variant):
     assert_flux_parity(f[sinks], ref, "clumpy sampled")
     mism = np.nonzero(np.any(c[sinks] != rc, axis=1))[0]
     assert len(mism) <= 2
-    # shadow: sinks just behind the occluder, seen from the clumps, are darker
-    # than sinks the same distance in front (a property at any size)
     assert st["refine_expansions"] > 0
 
 

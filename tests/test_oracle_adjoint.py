@@ -47,18 +47,56 @@ def test_adjoint_matches_replay_finite_differences(oracle_lib, theta, tau_ref, w
     for kind, idx, val in coords:
         ref = gl[idx] if kind == 0 else ga[idx]
         assert fd_agrees(R, w, kind, idx, val, ref), (kind, idx, ref)
+        # with every segment's bounding planes frozen too the loss is analytic, so
+        # the step of 1e-3 itself must agree: no retries at smaller steps
+        h = 1e-3 * val
+        fd = (R.loss(w, kind, idx, h, frozen_planes=True) -
+              R.loss(w, kind, idx, -h, frozen_planes=True)) / (2 * h)
+        assert abs(fd - ref) <= 1e-3 * abs(ref) + 1e-9, (kind, idx, fd, ref)
 
 
 def fd_agrees(R, w, kind, idx, val, ref, rel=1e-3, tol=1e-3):
-    """Central difference with step rel*val agrees with ref to tol (relative). The frozen
-    loss is piecewise smooth (a ray's entry or exit plane can switch inside the step), so
-    a step that straddles such a kink is retried with smaller steps (down to 1e-6)."""
+    """Central difference of the frozen-decision loss with step rel*val agrees with ref
+    to tol (relative). That loss is piecewise smooth: a ray's entry or exit plane in a
+    cell can switch inside the step (a kink). A step that fails must straddle such a
+    switch (the replay counts them), and a smaller step (down to 1e-6) must agree."""
     for r in (rel, rel / 10, rel / 100, rel / 1000):
         h = r * val
         fd = (R.loss(w, kind, idx, h) - R.loss(w, kind, idx, -h)) / (2 * h)
         if abs(fd - ref) <= tol * abs(ref) + 1e-9:
             return True
+        if R.kinks(kind, idx, h) == 0:
+            return False  # no plane switch inside the step: a real disagreement
     return False
+
+
+def test_replay_planes_and_kinks(oracle_lib):
+    # the frozen-plane loss equals the re-clipped loss wherever no bounding plane
+    # switches inside the step, and both equal the forward loss at h = 0
+    P = _problem(seed=47, n=2000, ns=30)
+    T = _tree(oracle_lib, P)
+    n = P["gas_xyz"].shape[1]
+    w = np.random.default_rng(2).standard_normal(n)
+    R = T.replay(0.75, 0.1)
+    base = R.loss(w)
+    assert abs(R.loss(w, frozen_planes=True) - base) <= 1e-13 * abs(base)
+    seen_kink = seen_clean = False
+    for j in range(P["src_xyz"].shape[1]):
+        for r in (1e-1, 1e-4):
+            h = r * float(P["src_lum"][j])
+            k = R.kinks(0, j, h)
+            a, b = R.loss(w, 0, j, h), R.loss(w, 0, j, h, frozen_planes=True)
+            if k == 0:
+                seen_clean = True
+                assert abs(a - b) <= 1e-12 * abs(base), (j, r)
+            else:
+                seen_kink = True
+    assert seen_kink and seen_clean
+    # an absorption coefficient moves no ray: no kinks, and both losses agree
+    for i in (0, 77, 1999):
+        h = 0.5 * float(P["alpha"][i])
+        assert R.kinks(1, i, h) == 0
+        assert abs(R.loss(w, 1, i, h) - R.loss(w, 1, i, h, frozen_planes=True)) <= 1e-13 * abs(base)
 
 
 def test_adjoint_euler_identities(oracle_lib):
