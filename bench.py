@@ -355,8 +355,9 @@ def _bench_batched(args, sm_mhz):
     peak, peak_kind = _peaks()
     dev_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     prof = _kernel_profile("walk_warp_batched_kernel_issue.json")
-    if prof is not None and prof.get("launch_shape") != shape:
-        prof = None  # the capture was of another launch shape
+    if prof is not None and prof.get("launch_shape", {}).get("walk_variant") != \
+            shape.get("walk_variant"):
+        prof = None  # the capture was of another walk variant
     res = {"workload": f"{len(trees)} boxes, {n} sinks (2^12..2^17 each), theta 0.75, tau_ref 0.1",
            "graph_fluxes_per_s": n / (min(t_graph) * 1e-3),
            "sequential_fluxes_per_s": n / (min(t_seq) * 1e-3),
@@ -368,6 +369,8 @@ def _bench_batched(args, sm_mhz):
            "roofline": _issue_roofline(prof, n, t_rep, sm_mhz, dev_sm, alg_bytes, peak,
                                        peak_kind, "walk_warp_batched_kernel (persistent, "
                                        "graph replay)")}
+    if prof is not None:
+        res["roofline"]["captured_launch_shape"] = prof.get("launch_shape")
     B.free()
     for t in trees:
         t.free()
@@ -434,6 +437,40 @@ def _bench_termination(args, P, g):
             "speedup": min(plain) / min(stop),
             "rays_terminated_frac": st["rays_terminated"] / max(st["interactions"], 1),
             "median_rel_change": float(rel.median()), "bound_holds": ok}
+
+
+def _bench_topdown(args, P, g):
+    """The top-down ray walk (ray_walk = 1; Sec. 3.1.3, Sec. 4) against the paper's
+    bottom-up walk on the workload and on an optically thin copy (every absorption
+    coefficient / 16): the walk times (no counters), segments and cells clipped per
+    sink, and each walk's RMS and largest fractional error against full refinement
+    (tau_ref = 0, where both walks sum the same leaves) on 65536 seeded sinks."""
+    import torch
+    from paper_1902_08083_gb300 import trevr
+    stream = torch.cuda.current_stream()
+    n = int(P["gas_xyz"].shape[1])
+    sample = torch.from_numpy(workloads.sink_sample(n, 1 << 16, seed=21)).to(g["alpha"].device)
+    kw = dict(lo=P["lo"], side=P["side"], bucket=P["bucket"])
+    th, tr = P["theta"], P["tau_ref"]
+    res = {"sample_sinks": 1 << 16}
+    for name, scale in (("workload", 1.0), ("thin_alpha_over_16", 1.0 / 16.0)):
+        alpha = (g["alpha"] * scale).contiguous()
+        tree = trevr.build_tree(g["gas_xyz"], alpha, g["src_xyz"], g["src_lum"], **kw)
+        ref = trevr.compute_flux(tree, th, 0.0, sink_idx=sample).double()
+        out = {}
+        for walk, rw in (("bottom_up", 0), ("top_down", 1)):
+            F, st = trevr.compute_flux(tree, th, tr, stats=True, ray_walk=rw)
+            ms = _time_ms(lambda: trevr.compute_flux(tree, th, tr, out=F, ray_walk=rw),
+                          args.steps, stream)
+            e = (F[sample].double() - ref) / ref
+            out[walk] = {"walk_ms": min(ms), "segments_per_sink": st["segments"] / n,
+                         "cells_clipped_per_sink": st["cells_clipped"] / n,
+                         "rms_error_vs_full_refinement": float(torch.sqrt(torch.mean(e * e))),
+                         "max_error_vs_full_refinement": float(e.abs().max())}
+        out["speedup"] = out["bottom_up"]["walk_ms"] / out["top_down"]["walk_ms"]
+        res[name] = out
+        tree.free()
+    return res
 
 
 def _bench_bands(args, P, g):
@@ -677,6 +714,7 @@ def run_ours(args):
         line["batched"] = _bench_batched(args, sm_mhz)
         line["adjoint"] = _bench_adjoint(args)
         line["terminated"] = _bench_termination(args, P, g)
+        line["top_down"] = _bench_topdown(args, P, g)
         line["bands"] = _bench_bands(args, P, g)
         line["sub_bucket"] = _bench_sub_bucket(args)
         if args.glass:

@@ -89,6 +89,18 @@ typedef struct {
                            mean. The receiving particle is left out of that sum. 0 = off.
                            Only trevr_compute_flux accepts it, without bg_radius or
                            tau_stop. */
+    int ray_walk;       /* 0: the paper's ray walk (Sec. 2.2.2, 3.1.3): the segments are
+                           the sink's bucket S, the source cell C and the siblings of the
+                           cells on the two paths up to their lowest common ancestor A,
+                           each refined by Eq. refcrit. 1: the top-down ray walk that the
+                           paper names as an alternative (Sec. 3.1.3, last paragraph of
+                           "Refinement Criterion"; Sec. 4): the ray starts as the single
+                           segment A and only Eq. refcrit splits it, so a ray costs one
+                           segment where the medium has no spread of absorption. Its
+                           segments are unions of the paper's walk's; tau_ref <= 0 gives
+                           the same cells. Only trevr_compute_flux accepts 1, without
+                           bg_radius, tau_stop or sub_bucket; it runs the merged-ray walk
+                           (walk_variant 3). */
 } trevr_params;
 
 /* Totals over the sinks of one call, and timings (ms, CUDA events). */
@@ -302,7 +314,8 @@ int trevr_tree_info(const trevr_tree* t, long long* n_nodes, int* max_depth, lon
  *   parent   int32 (0 for the root).   depth int32.
  *   glo, ghi 3 int32 per cell: integer box on the 2^21 grid, [glo, ghi).
  *   abar     fp32 mean absorption;  dalpha fp32 alpha_max - alpha_min;
- *   lum      fp32 total luminosity;  cen 3 fp32 centre of luminosity;
+ *   lum      fp32 total luminosity;  cen 3 fp32 centre of luminosity, relative to
+ *            the domain's lower corner (the frame the walk computes in: x - lo);
  *   l2       fp32 squared distance from the centre to the furthest vertex.
  *   src_first, src_count  int32 range of each cell in the sorted sources;
  *   src_order n_src int32 caller index of the k-th sorted source.

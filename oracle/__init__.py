@@ -92,6 +92,10 @@ def _load():
         lib.orc_sink_interactions.restype = i64
         lib.orc_ray_tau.argtypes = [P, i64, i64, P, f32, P, P]
         lib.orc_ray_tau.restype = ctypes.c_double
+        lib.orc_ray_tau_walk.argtypes = [P, i64, i64, P, f32, ctypes.c_int, P, P]
+        lib.orc_ray_tau_walk.restype = ctypes.c_double
+        lib.orc_flux_topdown.argtypes = [P, P, i64, f32, f32, P, P, ctypes.c_int]
+        lib.orc_flux_topdown.restype = ctypes.c_int
         lib.orc_adjoint.argtypes = [P, P, i64, P, f32, f32, P, P, ctypes.c_int]
         lib.orc_adjoint.restype = ctypes.c_int
         lib.orc_replay_record.argtypes = [P, P, i64, f32, f32, ctypes.POINTER(P)]
@@ -361,15 +365,33 @@ class OracleTree:
             raise OracleError(ORC_ERR_NO_MEMORY)
         return {k: v[:n] for k, v in out.items()}
 
-    def ray_tau(self, sink, node, q, tau_ref):
+    def ray_tau(self, sink, node, q, tau_ref, topdown=False):
         """Optical depth (tau, summed segment length, segment count) of the method's ray
-        from sink (caller index) to point q inside node."""
+        from sink (caller index) to point q inside node; topdown selects the top-down
+        ray walk instead of the paper's bottom-up one."""
         q = _f32(q)
         ls = ctypes.c_double()
         ns = ctypes.c_int64()
-        t = self._lib.orc_ray_tau(self._h, int(sink), int(node), _ptr(q), float(tau_ref),
-                                  ctypes.byref(ls), ctypes.byref(ns))
+        t = self._lib.orc_ray_tau_walk(self._h, int(sink), int(node), _ptr(q), float(tau_ref),
+                                       int(bool(topdown)), ctypes.byref(ls), ctypes.byref(ns))
         return t, ls.value, ns.value
+
+    def flux_topdown(self, theta, tau_ref, sinks=None, nthreads=0, with_counters=False):
+        """FP64 flux with the top-down ray walk (the ray starts as one segment in the
+        lowest common ancestor of the sink's bucket and the source cell, and only the
+        refinement criterion splits it). Returns flux, or (flux, counters[n,4]) with
+        with_counters (interactions, segments, visited source nodes, refinements)."""
+        if sinks is None:
+            sinks = np.arange(self.n_gas, dtype=np.int64)
+        sinks = np.ascontiguousarray(sinks, dtype=np.int64)
+        n = sinks.shape[0]
+        flux = np.zeros(n)
+        cnt = np.zeros((n, 4), np.int64) if with_counters else None
+        rc = self._lib.orc_flux_topdown(self._h, _ptr(sinks), n, float(theta), float(tau_ref),
+                                        _ptr(flux), _ptr(cnt), int(nthreads))
+        if rc != ORC_OK:
+            raise OracleError(rc)
+        return (flux, cnt) if with_counters else flux
 
     def adjoint(self, theta, tau_ref, grad_flux, sinks=None, nthreads=0):
         """FP64 gradients (grad_lum[n_src], grad_alpha[n_gas], caller order) of a loss with

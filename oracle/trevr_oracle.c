@@ -14,8 +14,12 @@
  * coincident-source skip -- are taken in IEEE fp32 with the operation
  * sequences written out below, because those decisions turn floating point
  * into integers and both implementations must take them in the same
- * precision. The FP64 relative margin of each decision is recorded so a
- * reader can see how close each call was.
+ * precision. They work in coordinates relative to the domain's lower corner
+ * (u = x - lo, cell planes g*h, rounded once each in fp32), so that their
+ * rounding depends on the size of the domain and not on its distance from the
+ * origin. The FP64 values use the positions and planes as given (lo + g*h).
+ * The FP64 relative margin of each decision is recorded so a reader can see
+ * how close each call was.
  *
  * Build: gcc -O2 -fopenmp -ffp-contract=off -fPIC -shared (contraction must
  * stay off so every fp32 expression rounds after each operation).
@@ -76,6 +80,9 @@ typedef struct {
     int64_t *rank;    /* rank[caller index] = sorted position */
     int64_t *leaf_of; /* leaf node of the i-th sorted particle */
     float *px, *py, *pz, *alpha, *w;
+    /* the same positions relative to the domain's lower corner, u = x - lo in fp32:
+       the frame of every fp32 decision (the cell planes are g * h in it) */
+    float *ux, *uy, *uz;
 
     /* nodes */
     int64_t *first, *count, *parent, *lower; /* lower child (upper = next subtree) */
@@ -91,6 +98,7 @@ typedef struct {
     /* sources, sorted by (first particle of their leaf, caller index) */
     int64_t *src_order, *src_leaf;
     float *sx, *sy, *sz, *slum;
+    float *usx, *usy, *usz; /* source positions relative to lo (fp32), as ux */
 
     /* several bands (orc_build_bands; nb = 0 otherwise): per cell and band the mean
        absorption and the luminosity, per sorted source and band the luminosity */
@@ -232,8 +240,11 @@ static int64_t build_rec(orc_tree *T, int64_t i, int64_t j, const int32_t glo[3]
 
 static int split_axis_of(int32_t b) { return (62 - b) % 3; }
 
-/* fp32 world coordinate of grid plane g: lo + g*h, h = side * 2^-21. */
-static float world32(float lo, float h, int32_t g) { return lo + (float)g * h; }
+/* fp32 coordinate of grid plane g relative to the domain's lower corner: g*h,
+   h = side * 2^-21. Every fp32 decision works in this frame (positions u = x - lo),
+   so a plane's rounding depends on the domain's size only, not on its offset from
+   the origin; far from the origin, lo + g*h in fp32 would merge distinct planes. */
+static float rel32(float h, int32_t g) { return (float)g * h; }
 
 /* ------------------------------------------------------------------------ */
 /* Cell moments (Sec. 2.2.3, 2.3).                                           */
@@ -278,16 +289,23 @@ static void node_moments(orc_tree *T)
     }
     /* sources: total luminosity and centre of luminosity (Sec. 2.2.1) */
     for (int64_t X = 0; X < nn; ++X) {
-        double sl = 0.0, sy[3] = {0.0, 0.0, 0.0};
+        double sl = 0.0, sy[3] = {0.0, 0.0, 0.0}, su[3] = {0.0, 0.0, 0.0};
         for (int64_t s = T->src_first[X]; s < T->src_first[X] + T->src_count[X]; ++s) {
             double Lj = (double)T->slum[s];
             sl += Lj;
             sy[0] += Lj * (double)T->sx[s];
             sy[1] += Lj * (double)T->sy[s];
             sy[2] += Lj * (double)T->sz[s];
+            su[0] += Lj * (double)T->usx[s];
+            su[1] += Lj * (double)T->usy[s];
+            su[2] += Lj * (double)T->usz[s];
         }
         T->L[X] = sl;
-        for (int d = 0; d < 3; ++d) T->cen[X][d] = sl > 0.0 ? sy[d] / sl : 0.0;
+        for (int d = 0; d < 3; ++d) {
+            T->cen[X][d] = sl > 0.0 ? sy[d] / sl : 0.0;
+            /* the decisions' centre: from the sources' fp32 relative positions */
+            T->cen32[X][d] = sl > 0.0 ? (float)(su[d] / sl) : 0.0f;
+        }
     }
     /* fp32 copies used by the decisions, and l = furthest vertex from the centroid */
     for (int64_t X = 0; X < nn; ++X) {
@@ -295,9 +313,8 @@ static void node_moments(orc_tree *T)
         T->dalpha32[X] = (float)(T->amax[X] - T->amin[X]);
         T->L32[X] = (float)T->L[X];
         for (int d = 0; d < 3; ++d) {
-            T->cen32[X][d] = (float)T->cen[X][d];
-            T->blo32[X][d] = world32(T->lo32[d], T->h32, T->glo[X][d]);
-            T->bhi32[X][d] = world32(T->lo32[d], T->h32, T->ghi[X][d]);
+            T->blo32[X][d] = rel32(T->h32, T->glo[X][d]);
+            T->bhi32[X][d] = rel32(T->h32, T->ghi[X][d]);
         }
         float l2 = 0.0f;
         double l2d = 0.0;
@@ -386,6 +403,9 @@ int orc_build(const float *gas_x, const float *gas_y, const float *gas_z, const 
     ALLOC(T->px, n_gas);
     ALLOC(T->py, n_gas);
     ALLOC(T->pz, n_gas);
+    ALLOC(T->ux, n_gas);
+    ALLOC(T->uy, n_gas);
+    ALLOC(T->uz, n_gas);
     ALLOC(T->alpha, n_gas);
     ALLOC(T->w, n_gas);
     ALLOC(T->first, cap);
@@ -420,6 +440,9 @@ int orc_build(const float *gas_x, const float *gas_y, const float *gas_z, const 
     ALLOC(T->sx, n_src);
     ALLOC(T->sy, n_src);
     ALLOC(T->sz, n_src);
+    ALLOC(T->usx, n_src);
+    ALLOC(T->usy, n_src);
+    ALLOC(T->usz, n_src);
     ALLOC(T->slum, n_src);
 
     {
@@ -450,6 +473,9 @@ int orc_build(const float *gas_x, const float *gas_y, const float *gas_z, const 
             T->px[i] = gas_x[o];
             T->py[i] = gas_y[o];
             T->pz[i] = gas_z[o];
+            T->ux[i] = gas_x[o] - T->lo32[0];
+            T->uy[i] = gas_y[o] - T->lo32[1];
+            T->uz[i] = gas_z[o] - T->lo32[2];
             T->alpha[i] = alpha[o];
             T->w[i] = weight ? weight[o] : 1.0f;
         }
@@ -498,6 +524,9 @@ int orc_build(const float *gas_x, const float *gas_y, const float *gas_z, const 
             T->sx[s] = src_x[o];
             T->sy[s] = src_y[o];
             T->sz[s] = src_z[o];
+            T->usx[s] = src_x[o] - T->lo32[0];
+            T->usy[s] = src_y[o] - T->lo32[1];
+            T->usz[s] = src_z[o] - T->lo32[2];
             T->slum[s] = src_lum[o];
         }
         free(kv);
@@ -603,7 +632,8 @@ int orc_build_bands(const float *gas_x, const float *gas_y, const float *gas_z,
 void orc_tree_free(orc_tree *T)
 {
     if (!T) return;
-    void *ptrs[] = {T->key, T->perm, T->rank, T->leaf_of, T->px, T->py, T->pz, T->alpha, T->w,
+    void *ptrs[] = {T->key, T->perm, T->rank, T->leaf_of, T->px, T->py, T->pz, T->ux, T->uy,
+                    T->uz, T->usx, T->usy, T->usz, T->alpha, T->w,
                     T->first, T->count, T->parent, T->lower, T->upper, T->split_bit, T->depth,
                     T->glo, T->ghi, T->W, T->abar, T->amin_d, T->amax_d, T->amin, T->amax, T->L,
                     T->cen, T->lrad, T->abar32, T->dalpha32, T->L32, T->cen32, T->l2_32, T->blo32,
@@ -960,6 +990,32 @@ static void ray_tau(const orc_tree *T, const ray_t *R, int64_t S, int64_t C, flo
     }
 }
 
+/*
+ * Top-down ray walk (Sec. 3.1.3, last paragraph of "Refinement Criterion"; Sec. 4,
+ * Discussion). The paper's own walk above goes up from the sink's bucket and from
+ * the source cell, and so always splits the ray into the cells along both paths;
+ * the paper notes that a walk going down the tree instead would rest more, or
+ * solely, on the refinement criterion, and could scale better than N log^2 N in
+ * optically thin media. Here the ray starts as one segment in A, the lowest common
+ * ancestor of S and C (the smallest cell that holds the whole ray; every cell
+ * above it holds the ray whole too), and seg() refines it by Eq. refcrit alone:
+ * a cell whose (alpha_max - alpha_min) l exceeds tau_ref is replaced by its two
+ * children, down to the buckets. tau_ref <= 0 refines to the buckets everywhere,
+ * as the bottom-up walk does. S == C gives the single segment S, as there.
+ */
+static void ray_tau_topdown(const orc_tree *T, const ray_t *R, int64_t S, int64_t C, float tau_ref,
+                            counters_t *c, raysum_t *rs)
+{
+    int64_t u = S, v = C;
+    while (T->depth[u] > T->depth[v]) u = T->parent[u];
+    while (T->depth[v] > T->depth[u]) v = T->parent[v];
+    while (u != v) {
+        u = T->parent[u];
+        v = T->parent[v];
+    }
+    seg(T, R, u, tau_ref, c, rs);
+}
+
 typedef struct {
     int64_t node;  /* C */
     double q[3];   /* pseudo-source position */
@@ -989,9 +1045,10 @@ typedef struct {
     float tau_stop;   /* > 0: early ray termination (Sec. 4) */
     int sub_bucket;   /* particle trace below the buckets (Sec. 2.2.3, 3.1.3) */
     nsum_t *bandF;    /* per-band flux accumulators (trees with bands) */
+    int topdown;      /* 1: the top-down ray walk (ray_tau_topdown), 0: bottom-up */
 } walkopt_t;
 
-static const walkopt_t NO_OPTS = {0.0f, 0.0f, 0, NULL};
+static const walkopt_t NO_OPTS = {0.0f, 0.0f, 0, NULL, 0};
 
 /* One pseudo-source (L at q, inside node C) seen from sorted particle i.
    tau_stop > 0: early ray termination (Sec. 4, proposed there). The optical depth
@@ -1011,13 +1068,15 @@ static double contribute_m(const orc_tree *T, int64_t i, int64_t S, int64_t C, c
     memset(&R, 0, sizeof(R));
     R.sink = i;
     R.sub = o->sub_bucket;
-    R.p[0] = T->px[i];
-    R.p[1] = T->py[i];
-    R.p[2] = T->pz[i];
+    R.p[0] = T->ux[i];
+    R.p[1] = T->uy[i];
+    R.p[2] = T->uz[i];
+    R.P[0] = (double)T->px[i];
+    R.P[1] = (double)T->py[i];
+    R.P[2] = (double)T->pz[i];
     for (int k = 0; k < 3; ++k) {
         R.d[k] = q32[k] - R.p[k];
         R.inv[k] = R.d[k] != 0.0f ? 1.0f / R.d[k] : 0.0f;
-        R.P[k] = (double)R.p[k];
         R.D[k] = q64[k] - R.P[k];
     }
     float s2 = R.d[0] * R.d[0] + R.d[1] * R.d[1] + R.d[2] * R.d[2];
@@ -1027,7 +1086,10 @@ static double contribute_m(const orc_tree *T, int64_t i, int64_t S, int64_t C, c
     R.LEN = sqrt(S2);
     raysum_t rs;
     memset(&rs, 0, sizeof(rs));
-    ray_tau(T, &R, S, C, tau_ref, c, &rs);
+    if (o->topdown)
+        ray_tau_topdown(T, &R, S, C, tau_ref, c, &rs);
+    else
+        ray_tau(T, &R, S, C, tau_ref, c, &rs);
     double tau = nsum_get(&rs.tau);
     const int cut = tau_stop > 0.0f && tau > (double)tau_stop;
     /* Eq. simpint: I = L exp(-tau) / (4 pi s^2) */
@@ -1088,7 +1150,7 @@ static int64_t leaf_of_point_clamped(const orc_tree *T, const float q[3])
     const float scale = domain_scale32(T->side32);
     uint32_t g[3];
     for (int d = 0; d < 3; ++d) {
-        float t = (q[d] - T->lo32[d]) * scale;
+        float t = q[d] * scale; /* q relative to lo */
         if (!(t >= 0.0f)) t = 0.0f;
         uint32_t v = (uint32_t)t;
         g[d] = v > (uint32_t)(GRID_MAX - 1) ? (uint32_t)(GRID_MAX - 1) : v;
@@ -1101,9 +1163,9 @@ static int64_t leaf_of_point_clamped(const orc_tree *T, const float q[3])
  * around the centre of the domain, and a merged cell's centre of luminosity,
  * which lies inside the sphere, is moved radially onto it before the ray is
  * traced; the ray then ends in the leaf that holds the moved point. fp32
- * position (it drives the decisions): d = c - o; s = sqrt((dx^2 + dy^2) + dz^2);
- * k = R / s; q = o + d * k, with o = lo + side * 0.5. A centroid at the centre
- * itself is not moved.
+ * position (it drives the decisions), relative to lo like every fp32 decision:
+ * d = c - o; s = sqrt((dx^2 + dy^2) + dz^2); k = R / s; q = o + d * k, with the
+ * centre o = side * 0.5. A centroid at the centre itself is not moved.
  */
 static void bg_project(const orc_tree *T, const float c32[3], const double c64[3], float R,
                        float q32[3], double q64[3])
@@ -1111,7 +1173,7 @@ static void bg_project(const orc_tree *T, const float c32[3], const double c64[3
     float o[3], d[3];
     double O[3], D[3];
     for (int k = 0; k < 3; ++k) {
-        o[k] = T->lo32[k] + T->side32 * 0.5f;
+        o[k] = T->side32 * 0.5f; /* the centre, relative to lo */
         d[k] = c32[k] - o[k];
         O[k] = T->lo[k] + 0.5 * T->side;
         D[k] = c64[k] - O[k];
@@ -1131,7 +1193,7 @@ static double sink_flux_m(const orc_tree *T, int64_t i, float theta, float tau_r
     const float theta2 = theta * theta;
     const float smin = 1e-12f * T->side32;
     const float smin2 = smin * smin;
-    const float p[3] = {T->px[i], T->py[i], T->pz[i]};
+    const float p[3] = {T->ux[i], T->uy[i], T->uz[i]};
     const int64_t S = T->leaf_of[i];
     nsum_t F = {0.0, 0.0};
     int64_t stack[MAXDEPTH + 2];
@@ -1170,7 +1232,7 @@ static double sink_flux_m(const orc_tree *T, int64_t i, float theta, float tau_r
         } else if (T->split_bit[X] < 0) {
             for (int64_t s = T->src_first[X]; s < T->src_first[X] + T->src_count[X]; ++s) {
                 if (!(T->slum[s] > 0.0f)) continue;
-                const float q32[3] = {T->sx[s], T->sy[s], T->sz[s]};
+                const float q32[3] = {T->usx[s], T->usy[s], T->usz[s]};
                 const double q64[3] = {(double)T->sx[s], (double)T->sy[s], (double)T->sz[s]};
                 nsum_add(&F, contribute_m(T, i, S, X, q32, q64, (double)T->slum[s], tau_ref, smin2,
                                           c, log, s, mom, o));
@@ -1315,6 +1377,36 @@ int orc_flux_terminated(const orc_tree *T, const int64_t *sinks, int64_t n_sink,
     return ORC_OK;
 }
 
+/* Flux with the top-down ray walk (ray_tau_topdown). counters (nullable) gets 4
+   int64 per sink as in orc_flux: interactions, segments, visited source nodes and
+   refinements. */
+int orc_flux_topdown(const orc_tree *T, const int64_t *sinks, int64_t n_sink, float theta,
+                     float tau_ref, double *flux, int64_t *counters, int nthreads)
+{
+    if (T->nb > 1) return ORC_ERR_INVALID_ARGUMENT; /* a tree with bands: orc_flux_bands */
+    if (!(theta >= 0.0f) || !isfinite(theta) || isnan(tau_ref)) return ORC_ERR_INVALID_ARGUMENT;
+    for (int64_t k = 0; k < n_sink; ++k)
+        if (sinks[k] < 0 || sinks[k] >= T->n_gas) return ORC_ERR_INVALID_ARGUMENT;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t k = 0; k < n_sink; ++k) {
+        counters_t c;
+        memset(&c, 0, sizeof(c));
+        c.margin = INFINITY;
+        const walkopt_t o = {0.0f, 0.0f, 0, NULL, 1};
+        flux[k] = sink_flux_m(T, T->rank[sinks[k]], theta, tau_ref, &c, NULL, NULL, &o);
+        if (counters) {
+            counters[4 * k + 0] = c.interactions;
+            counters[4 * k + 1] = c.segments;
+            counters[4 * k + 2] = c.visited;
+            counters[4 * k + 3] = c.refinements;
+        }
+    }
+    return ORC_OK;
+}
+
 /* Flux of every band of a tree built by orc_build_bands: flux[b * n_sink + k].
    counters (nullable): 4 int64 per sink as in orc_flux. */
 int orc_flux_bands(const orc_tree *T, const int64_t *sinks, int64_t n_sink, float theta,
@@ -1436,20 +1528,24 @@ int64_t orc_sink_interactions(const orc_tree *T, int64_t sink, float theta, floa
 }
 
 /* Optical depth of the ray from sorted particle (caller index) sink to the
-   point q inside node C, with the segment set of the method. */
-double orc_ray_tau(const orc_tree *T, int64_t sink, int64_t C, const float q[3], float tau_ref,
-                   double *len_sum, int64_t *nseg)
+   point q inside node C, with the segment set of the bottom-up walk (topdown = 0)
+   or of the top-down walk (topdown = 1). */
+double orc_ray_tau_walk(const orc_tree *T, int64_t sink, int64_t C, const float q[3],
+                        float tau_ref, int topdown, double *len_sum, int64_t *nseg)
 {
     int64_t i = T->rank[sink];
     ray_t R;
     memset(&R, 0, sizeof(R));
-    R.p[0] = T->px[i];
-    R.p[1] = T->py[i];
-    R.p[2] = T->pz[i];
+    R.p[0] = T->ux[i];
+    R.p[1] = T->uy[i];
+    R.p[2] = T->uz[i];
+    R.P[0] = (double)T->px[i];
+    R.P[1] = (double)T->py[i];
+    R.P[2] = (double)T->pz[i];
     for (int k = 0; k < 3; ++k) {
-        R.d[k] = q[k] - R.p[k];
+        const float qu = q[k] - T->lo32[k]; /* q is given in world coordinates */
+        R.d[k] = qu - R.p[k];
         R.inv[k] = R.d[k] != 0.0f ? 1.0f / R.d[k] : 0.0f;
-        R.P[k] = (double)R.p[k];
         R.D[k] = (double)q[k] - R.P[k];
     }
     R.len = sqrtf(R.d[0] * R.d[0] + R.d[1] * R.d[1] + R.d[2] * R.d[2]);
@@ -1459,10 +1555,19 @@ double orc_ray_tau(const orc_tree *T, int64_t sink, int64_t C, const float q[3],
     c.margin = INFINITY;
     raysum_t rs;
     memset(&rs, 0, sizeof(rs));
-    ray_tau(T, &R, T->leaf_of[i], C, tau_ref, &c, &rs);
+    if (topdown)
+        ray_tau_topdown(T, &R, T->leaf_of[i], C, tau_ref, &c, &rs);
+    else
+        ray_tau(T, &R, T->leaf_of[i], C, tau_ref, &c, &rs);
     if (len_sum) *len_sum = rs.len_sum;
     if (nseg) *nseg = rs.nseg;
     return nsum_get(&rs.tau);
+}
+
+double orc_ray_tau(const orc_tree *T, int64_t sink, int64_t C, const float q[3], float tau_ref,
+                   double *len_sum, int64_t *nseg)
+{
+    return orc_ray_tau_walk(T, sink, C, q, tau_ref, 0, len_sum, nseg);
 }
 
 /* Leaf holding the grid point of (x,y,z) (same quantisation as the keys). */
@@ -1585,13 +1690,15 @@ static void make_ray(const orc_tree *T, int64_t i, const float q32[3], const dou
 {
     memset(R, 0, sizeof(*R));
     R->sink = i;
-    R->p[0] = T->px[i];
-    R->p[1] = T->py[i];
-    R->p[2] = T->pz[i];
+    R->p[0] = T->ux[i];
+    R->p[1] = T->uy[i];
+    R->p[2] = T->uz[i];
+    R->P[0] = (double)T->px[i];
+    R->P[1] = (double)T->py[i];
+    R->P[2] = (double)T->pz[i];
     for (int k = 0; k < 3; ++k) {
         R->d[k] = q32[k] - R->p[k];
         R->inv[k] = R->d[k] != 0.0f ? 1.0f / R->d[k] : 0.0f;
-        R->P[k] = (double)R->p[k];
         R->D[k] = q64[k] - R->P[k];
     }
     R->len = sqrtf(R->d[0] * R->d[0] + R->d[1] * R->d[1] + R->d[2] * R->d[2]);
@@ -1646,7 +1753,7 @@ static void adj_sink(const orc_tree *T, int64_t i, float theta, float tau_ref, d
     const float theta2 = theta * theta;
     const float smin = 1e-12f * T->side32;
     const float smin2 = smin * smin;
-    const float p[3] = {T->px[i], T->py[i], T->pz[i]};
+    const float p[3] = {T->ux[i], T->uy[i], T->uz[i]};
     const int64_t S = T->leaf_of[i];
     int64_t stack[MAXDEPTH + 2];
     int sp = 0;
@@ -1665,7 +1772,7 @@ static void adj_sink(const orc_tree *T, int64_t i, float theta, float tau_ref, d
         } else if (T->split_bit[X] < 0) {
             for (int64_t s = T->src_first[X]; s < T->src_first[X] + T->src_count[X]; ++s) {
                 if (!(T->slum[s] > 0.0f)) continue;
-                const float q32[3] = {T->sx[s], T->sy[s], T->sz[s]};
+                const float q32[3] = {T->usx[s], T->usy[s], T->usz[s]};
                 const double q64[3] = {(double)T->sx[s], (double)T->sy[s], (double)T->sz[s]};
                 adj_interaction(T, i, S, X, q32, q64, (double)T->slum[s], tau_ref, smin2, g, s,
                                 acc);
@@ -1808,7 +1915,7 @@ int orc_replay_record(const orc_tree *T, const int64_t *sinks, int64_t n_sink, f
         int64_t i = T->rank[sinks[k]];
         r->sink_i[k] = i;
         r->ia_start[k] = rb.n;
-        const float p[3] = {T->px[i], T->py[i], T->pz[i]};
+        const float p[3] = {T->ux[i], T->uy[i], T->uz[i]};
         const int64_t S = T->leaf_of[i];
         int64_t stack[MAXDEPTH + 2];
         int sp = 0;
@@ -1826,7 +1933,7 @@ int orc_replay_record(const orc_tree *T, const int64_t *sinks, int64_t n_sink, f
             } else if (T->split_bit[X] < 0) {
                 for (int64_t s = T->src_first[X]; s < T->src_first[X] + T->src_count[X]; ++s) {
                     if (!(T->slum[s] > 0.0f)) continue;
-                    const float q32[3] = {T->sx[s], T->sy[s], T->sz[s]};
+                    const float q32[3] = {T->usx[s], T->usy[s], T->usz[s]};
                     const double q64[3] = {(double)T->sx[s], (double)T->sy[s], (double)T->sz[s]};
                     rec_interaction(T, i, S, X, q32, q64, tau_ref, smin2, s, &rb);
                 }

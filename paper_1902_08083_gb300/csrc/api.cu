@@ -43,9 +43,11 @@ static WalkParams walk_params(const trevr_tree* t, const trevr_params* prm) {
   wp.bg_radius = prm->bg_radius;
   wp.tau_stop = prm->tau_stop > 0.0f ? prm->tau_stop : INFINITY;
   wp.sub_bucket = prm->sub_bucket;
-  // background sources, early termination and the sub-bucket trace are built into the
-  // merged-ray walk only
-  if (wp.bg_radius > 0.0f || prm->tau_stop > 0.0f || prm->sub_bucket) wp.variant = 3;
+  wp.topdown = prm->ray_walk;
+  // background sources, early termination, the sub-bucket trace and the top-down ray
+  // walk are built into the merged-ray walk only
+  if (wp.bg_radius > 0.0f || prm->tau_stop > 0.0f || prm->sub_bucket || prm->ray_walk)
+    wp.variant = 3;
   return wp;
 }
 
@@ -60,6 +62,7 @@ static bool params_ok(const trevr_params* prm) {
   if (!(prm->bg_radius >= 0.0f) || !std::isfinite(prm->bg_radius)) return false;
   if (!(prm->tau_stop >= 0.0f)) return false;
   if (prm->sub_bucket != 0 && prm->sub_bucket != 1) return false;
+  if (prm->ray_walk != 0 && prm->ray_walk != 1) return false;
   return true;
 }
 
@@ -160,7 +163,7 @@ int trevr_compute_flux_bands(const trevr_tree* t, const long long* sink_idx, lon
                              const trevr_params* prm, float* flux_out, int* sink_counters,
                              trevr_stats* stats, void* stream) {
   if (!t || !params_ok(prm) || t->n_bands < 1) return TREVR_ERR_INVALID_ARGUMENT;
-  if (prm->bg_radius > 0.0f || prm->tau_stop > 0.0f || prm->sub_bucket)
+  if (prm->bg_radius > 0.0f || prm->tau_stop > 0.0f || prm->sub_bucket || prm->ray_walk)
     return TREVR_ERR_INVALID_ARGUMENT;
   if (t->n_bands == 1)  // one band is the plain method on the same records
     return trevr_compute_flux(t, sink_idx, n_sink, prm, flux_out, sink_counters, stats, stream);
@@ -222,6 +225,8 @@ int trevr_compute_flux(const trevr_tree* t, const long long* sink_idx, long long
   if (n_sink < 0 || n_sink > (1ll << 30)) return TREVR_ERR_INVALID_ARGUMENT;
   if (prm->sub_bucket && (!t->nbr_first || prm->bg_radius > 0.0f || prm->tau_stop > 0.0f))
     return TREVR_ERR_INVALID_ARGUMENT;
+  if (prm->ray_walk && (prm->bg_radius > 0.0f || prm->tau_stop > 0.0f || prm->sub_bucket))
+    return TREVR_ERR_INVALID_ARGUMENT;
   if (stats) std::memset(stats, 0, sizeof(*stats));
   if (n_sink == 0) return TREVR_OK;
   if (!flux_out) return TREVR_ERR_INVALID_ARGUMENT;
@@ -275,7 +280,7 @@ int trevr_compute_flux_moments(const trevr_tree* t, const long long* sink_idx, l
                                float* press_out, void* stream) {
   if (!t || !params_ok(prm) || t->n_bands > 1) return TREVR_ERR_INVALID_ARGUMENT;
   if (n_sink < 0 || n_sink > (1ll << 30)) return TREVR_ERR_INVALID_ARGUMENT;
-  if (prm->bg_radius > 0.0f || prm->tau_stop > 0.0f || prm->sub_bucket)
+  if (prm->bg_radius > 0.0f || prm->tau_stop > 0.0f || prm->sub_bucket || prm->ray_walk)
     return TREVR_ERR_INVALID_ARGUMENT;
   if (n_sink == 0) return TREVR_OK;
   if (!flux_out || !fvec_out) return TREVR_ERR_INVALID_ARGUMENT;
@@ -303,7 +308,7 @@ int trevr_compute_flux_backward(const trevr_tree* t, const long long* sink_idx, 
   if (!t || !params_ok(prm) || t->n_bands > 1) return TREVR_ERR_INVALID_ARGUMENT;
   if (n_sink < 0 || n_sink > (1ll << 30)) return TREVR_ERR_INVALID_ARGUMENT;
   if (n_sink > 0 && !grad_flux) return TREVR_ERR_INVALID_ARGUMENT;
-  if (prm->bg_radius > 0.0f || prm->tau_stop > 0.0f || prm->sub_bucket)
+  if (prm->bg_radius > 0.0f || prm->tau_stop > 0.0f || prm->sub_bucket || prm->ray_walk)
     return TREVR_ERR_INVALID_ARGUMENT;
   if (n_sink > 0 && !sink_idx && n_sink != t->n_gas) return TREVR_ERR_INVALID_ARGUMENT;
   if ((t->n_src > 0 && !grad_lum) || !grad_alpha) return TREVR_ERR_INVALID_ARGUMENT;
@@ -401,7 +406,7 @@ static int batch_items(trevr_batch* B, int item) {
 int trevr_compute_flux_batched(trevr_batch* B, const trevr_params* prm, float* const* flux_out,
                                trevr_stats* stats, void* stream) {
   if (!B || !flux_out || !params_ok(prm)) return TREVR_ERR_INVALID_ARGUMENT;
-  if (prm->bg_radius > 0.0f || prm->tau_stop > 0.0f || prm->sub_bucket)
+  if (prm->bg_radius > 0.0f || prm->tau_stop > 0.0f || prm->sub_bucket || prm->ray_walk)
     return TREVR_ERR_INVALID_ARGUMENT;
   const int item = prm->sinks_per_warp > 0 ? prm->sinks_per_warp : 64;
   if (item % 32 != 0 || item > (1 << 20)) return TREVR_ERR_INVALID_ARGUMENT;
@@ -421,6 +426,7 @@ int trevr_compute_flux_batched(trevr_batch* B, const trevr_params* prm, float* c
   wp.bg_radius = 0.0f;
   wp.tau_stop = INFINITY;
   wp.sub_bucket = 0;
+  wp.topdown = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));

@@ -202,15 +202,19 @@ void radix_sort(unsigned long long* k, unsigned* v, int n, int bits, const SortS
 // ------------------------------------------------------------------------------------
 // Particle gather into Morton order
 // ------------------------------------------------------------------------------------
+// Sorted particles: position relative to the domain's lower corner (u = x - lo, one
+// fp32 rounding; the frame of every fp32 decision, in which the cell planes are
+// g * h), and alpha.
 __global__ void gather_particles_kernel(const float* __restrict__ xyz,
                                         const float* __restrict__ alpha,
-                                        const float* __restrict__ weight, int n,
+                                        const float* __restrict__ weight, int n, Domain32 D,
                                         const unsigned* __restrict__ order, float4* pos, float* w,
                                         int* perm, int* rank) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int o = (int)order[i];
-  pos[i] = make_float4(xyz[o], xyz[(size_t)n + o], xyz[2 * (size_t)n + o], alpha[o]);
+  pos[i] = make_float4(__fsub_rn(xyz[o], D.lo[0]), __fsub_rn(xyz[(size_t)n + o], D.lo[1]),
+                       __fsub_rn(xyz[2 * (size_t)n + o], D.lo[2]), alpha[o]);
   w[i] = weight ? weight[o] : 1.0f;
   perm[i] = o;
   rank[o] = i;
@@ -394,15 +398,17 @@ __global__ void src_leaf_kernel(const float* __restrict__ xyz, const float* __re
   vals[s] = (unsigned)s;
 }
 
+// sources sorted by leaf, positions relative to the domain's lower corner
 __global__ void gather_sources_kernel(const float* __restrict__ xyz, const float* __restrict__ lum,
-                                      int n_src, const unsigned* __restrict__ order,
+                                      int n_src, Domain32 D, const unsigned* __restrict__ order,
                                       const unsigned long long* __restrict__ leaf_first,
                                       const int* __restrict__ leaf_of, float4* src, int* src_order,
                                       int* src_leaf) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_src) return;
   int o = (int)order[k];
-  src[k] = make_float4(xyz[o], xyz[(size_t)n_src + o], xyz[2 * (size_t)n_src + o], lum[o]);
+  src[k] = make_float4(__fsub_rn(xyz[o], D.lo[0]), __fsub_rn(xyz[(size_t)n_src + o], D.lo[1]),
+                       __fsub_rn(xyz[2 * (size_t)n_src + o], D.lo[2]), lum[o]);
   src_order[k] = o;
   src_leaf[k] = leaf_of[(int)leaf_first[k]];  // the leaf that starts at that particle
 }
@@ -455,12 +461,11 @@ struct MomentArrays {
   float4* nB;
   float4* nS;
   float* nl2;
-  float lo[3], h;
+  float h;
 };
 
-__device__ __forceinline__ float world(float lo, float h, int g) {
-  return __fadd_rn(lo, __fmul_rn((float)g, h));
-}
+// a grid plane relative to the domain's lower corner: g * h, rounded once
+__device__ __forceinline__ float rel_plane(float h, int g) { return __fmul_rn((float)g, h); }
 
 __global__ void moments_level_kernel(MomentArrays A, int L) {
   const int begin = A.levels[2 * L], end = A.levels[2 * L + 1];
@@ -531,10 +536,8 @@ __global__ void moments_level_kernel(MomentArrays A, int L) {
     float c[3];
     for (int d = 0; d < 3; ++d) c[d] = m.L > 0.0 ? __double2float_rn(__ddiv_rn(m.LY[d], m.L)) : 0.0f;
     const int4 gl = A.nglo[X], gh = A.nghi[X];
-    const float blo[3] = {world(A.lo[0], A.h, gl.x), world(A.lo[1], A.h, gl.y),
-                          world(A.lo[2], A.h, gl.z)};
-    const float bhi[3] = {world(A.lo[0], A.h, gh.x), world(A.lo[1], A.h, gh.y),
-                          world(A.lo[2], A.h, gh.z)};
+    const float blo[3] = {rel_plane(A.h, gl.x), rel_plane(A.h, gl.y), rel_plane(A.h, gl.z)};
+    const float bhi[3] = {rel_plane(A.h, gh.x), rel_plane(A.h, gh.y), rel_plane(A.h, gh.z)};
     float l2 = 0.0f;
     for (int d = 0; d < 3; ++d) {
       float e = fmaxf(__fsub_rn(c[d], blo[d]), __fsub_rn(bhi[d], c[d]));
@@ -672,7 +675,7 @@ int build_tree_impl(const float* gas_xyz, const float* alpha, const float* weigh
                                                  t->status);
   note_launch();
   radix_sort(t->key, vals, n, 63, SS, s);
-  gather_particles_kernel<<<grid_for(n, 256), 256, 0, s>>>(gas_xyz, alpha, weight, n, vals,
+  gather_particles_kernel<<<grid_for(n, 256), 256, 0, s>>>(gas_xyz, alpha, weight, n, D, vals,
                                                             t->pos, t->w, t->perm, t->rank);
   note_launch();
   // 2. topology, top-down
@@ -718,7 +721,7 @@ int build_tree_impl(const float* gas_xyz, const float* alpha, const float* weigh
                                                        t->nfirst, skeys, svals, t->status);
     note_launch();
     radix_sort(skeys, svals, ns, 32, SS, s);
-    gather_sources_kernel<<<grid_for(ns, 256), 256, 0, s>>>(src_xyz, src_lum, ns, svals, skeys,
+    gather_sources_kernel<<<grid_for(ns, 256), 256, 0, s>>>(src_xyz, src_lum, ns, D, svals, skeys,
                                                              t->leaf_of, t->src, t->src_order,
                                                              t->src_leaf);
     note_launch();
@@ -760,7 +763,6 @@ int build_tree_impl(const float* gas_xyz, const float* alpha, const float* weigh
   MA.nB = t->nB;
   MA.nS = t->nS;
   MA.nl2 = t->nl2;
-  for (int d = 0; d < 3; ++d) MA.lo[d] = t->lo[d];
   MA.h = t->h;
   for (int L = max_depth; L >= 0; --L) {
     int m = levels[2 * L + 1] - levels[2 * L];

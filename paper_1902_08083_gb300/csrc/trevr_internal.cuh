@@ -175,6 +175,7 @@ struct WalkParams {
   float bg_radius;     // > 0: sources are background sources on this sphere (Sec. 2.2.4)
   float tau_stop;      // early ray termination threshold (+inf = off)
   int sub_bucket;      // sub-bucket particle trace (the tree has smoothing lengths)
+  int topdown;         // 1: top-down ray walk (a ray starts as its common ancestor cell)
 };
 // accumulators of the adjoint (FP64, zeroed by the caller)
 struct AdjointArgs {

@@ -12,7 +12,10 @@
 //     which case its children are used instead;
 //   * flux: sum of L exp(-tau) / (4 pi s^2) (Eq. simpint).
 // The decisions (opening angle, refinement, "does the ray touch the cell") are
-// evaluated with explicitly rounded fp32 operations in a fixed order.
+// evaluated with explicitly rounded fp32 operations in a fixed order. Positions,
+// centres of luminosity and cell planes are stored relative to the domain's lower
+// corner (planes g * h), so their fp32 rounding depends on the domain's size and not
+// on its offset from the origin.
 //
 // GPU form (sinks in Morton order, so the lanes of a warp are neighbours in space).
 //   * Variant 1 (walk_kernel): one lane per sink, a flat loop in which one
@@ -734,7 +737,12 @@ __device__ __forceinline__ float sub_bucket_tau_warp(const TreeView& T, int src,
 // optical depth over the shared segments, and F[b] gets band b's flux.
 // SUB: the sub-bucket particle trace for leaves whose own particles ask for
 // refinement (the sink's sorted index si is left out of the sum).
-template <bool ADJ, bool MOM, bool STOP = false, int NB = 1, bool SUB = false, bool CNT = true>
+// TD: the top-down ray walk (Sec. 3.1.3, Sec. 4): the ray's only base segment is the
+// common ancestor A = path[d*], and Eq. refcrit alone splits it through the same
+// refinement stack; without TD the base segments are C, the siblings up both paths
+// and S, as in the paper's walk.
+template <bool ADJ, bool MOM, bool STOP = false, int NB = 1, bool SUB = false, bool CNT = true,
+          bool TD = false>
 __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P, const bool on,
                                          const float px, const float py, const float pz,
                                          const int S, const int dS, const int* anc, int* rst,
@@ -751,6 +759,7 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
   const unsigned FULL = 0xffffffffu;
   float dx = 0.0f, dy = 0.0f, dz = 0.0f, s2 = 1.0f, len = 1.0f, ix = 0.0f, iy = 0.0f, iz = 0.0f;
   int nCs = 0, nSs = 0, nb = 0, dstar = 0;
+  int base1 = S;  // the base segment of a one-segment ray: S, or A for the top-down walk
   bool active = false;
   if (on) {
     dx = __fsub_rn(qx, px);
@@ -769,9 +778,14 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
         const int mn = dC < dS ? dC : dS;
         const unsigned long long m = on_path & ((2ull << mn) - 1ull);  // mn <= 62
         dstar = __ffsll((long long)~m) - 2;
-        nCs = dC - dstar - 1;
-        nSs = dS - dstar - 1;
-        nb = nCs + nSs + 2;
+        if (TD) {
+          nb = 1;
+          base1 = path[dstar];
+        } else {
+          nCs = dC - dstar - 1;
+          nSs = dS - dstar - 1;
+          nb = nCs + nSs + 2;
+        }
       }
     }
   }
@@ -867,7 +881,7 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
             slot = box + 1;
           }
         } else {
-          if (nb == 1) box = S;
+          if (nb == 1) box = base1;
           else if (b == 0) box = C;
           else if (b <= nCs) box = path[dC - b + 1] ^ 1;
           else if (b <= nCs + nSs) box = anc[dstar + 1 + (b - nCs)] ^ 1;
@@ -1008,7 +1022,7 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
 // q = o + d * (R / s); the ray then ends in the leaf that holds q, whose ancestors the
 // lane finds by descending the cut planes from the root and keeps for that ray.
 template <bool ADJ, bool MERGE, bool MOM = false, bool BG = false, bool STOP = false, int NB = 1,
-          bool SUB = false, bool CNT = true>
+          bool SUB = false, bool CNT = true, bool TD = false>
 __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P, const bool has,
                                           const int i, const float gk, WarpStack& ws,
                                           int* status, const AdjointArgs& J,
@@ -1060,11 +1074,11 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
         for (int d = 0; d <= mn && cpath[d] == anc[d]; ++d) onp |= 1ull << d;
         pp = cpath;
       }
-      warp_ray<ADJ, MOM, STOP, NB, SUB, CNT>(T, P, pnd, px, py, pz, S, dS, anc, rst, onp, pp, pC, pdC, pqx, pqy,
+      warp_ray<ADJ, MOM, STOP, NB, SUB, CNT, TD>(T, P, pnd, px, py, pz, S, dS, anc, rst, onp, pp, pC, pdC, pqx, pqy,
                          pqz, pL, psrc, gk, stack_limit, box_limit, status, J, cnt, F, mom,
                          i);
     } else {
-      warp_ray<ADJ, MOM, STOP, NB, SUB, CNT>(T, P, pnd, px, py, pz, S, dS, anc, rst, on_path, ws.path, pC, pdC,
+      warp_ray<ADJ, MOM, STOP, NB, SUB, CNT, TD>(T, P, pnd, px, py, pz, S, dS, anc, rst, on_path, ws.path, pC, pdC,
                          pqx, pqy, pqz, pL, psrc, gk, stack_limit, box_limit, status, J, cnt, F,
                          mom, i);
     }
@@ -1112,10 +1126,9 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
         pL = s.w;
         psrc = -1;
         if (BG) {
-          // move the centre of luminosity onto the sphere
-          const float ox = __fadd_rn(T.lo[0], __fmul_rn(T.side, 0.5f));
-          const float oy = __fadd_rn(T.lo[1], __fmul_rn(T.side, 0.5f));
-          const float oz = __fadd_rn(T.lo[2], __fmul_rn(T.side, 0.5f));
+          // move the centre of luminosity onto the sphere (coordinates relative to the
+          // domain's lower corner: the centre is side / 2)
+          const float ox = __fmul_rn(T.side, 0.5f), oy = ox, oz = ox;
           const float ddx = __fsub_rn(s.x, ox), ddy = __fsub_rn(s.y, oy), ddz = __fsub_rn(s.z, oz);
           const float sn = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(ddx, ddx), __fmul_rn(ddy, ddy)),
                                                 __fmul_rn(ddz, ddz)));
@@ -1131,7 +1144,7 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
           int g[3];
 #pragma unroll
           for (int d = 0; d < 3; ++d) {
-            float t = __fmul_rn(__fsub_rn(qq[d], T.lo[d]), scale);
+            float t = __fmul_rn(qq[d], scale);
             if (!(t >= 0.0f)) t = 0.0f;
             const unsigned v = __float2uint_rz(t);
             g[d] = (int)(v > (unsigned)(kGridMax - 1) ? (unsigned)(kGridMax - 1) : v);
@@ -1153,7 +1166,7 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
         }
       }
     } else if (accM) {
-      warp_ray<ADJ, MOM, STOP, NB, SUB, CNT>(T, P, acc, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX, s.x,
+      warp_ray<ADJ, MOM, STOP, NB, SUB, CNT, TD>(T, P, acc, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX, s.x,
                          s.y, s.z, s.w, -1, gk, stack_limit, box_limit, status, J, cnt, F, mom,
                          i);
     }
@@ -1176,7 +1189,7 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
               psrc = jj;
             }
           } else {
-            warp_ray<ADJ, MOM, STOP, NB, SUB, CNT>(T, P, opn, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX,
+            warp_ray<ADJ, MOM, STOP, NB, SUB, CNT, TD>(T, P, opn, px, py, pz, S, dS, anc, rst, on_path, ws.path, X, dX,
                                y.x, y.y, y.z, y.w, jj, gk, stack_limit, box_limit, status, J, cnt,
                                F, mom, i);
           }
@@ -1211,7 +1224,7 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
 // walks without counters fit 6 blocks (74 registers, no spills) instead of 4:
 // 245 ms against 262 ms for four bands on the clumpy workload.
 template <bool ADJ, bool MERGE, bool MOM = false, bool BG = false, bool STOP = false, int NB = 1,
-          bool SUB = false, bool CNT = true>
+          bool SUB = false, bool CNT = true, bool TD = false>
 __global__ void __launch_bounds__(128, SUB ? 4 : (NB > 1 ? (CNT ? 4 : 6) : (CNT ? 8 : 9))) walk_warp_kernel(TreeView T, const long long* sink_idx,
                                                         int n_sink, WalkParams P, SinkOut out,
                                                         unsigned long long* stats, int* status,
@@ -1235,7 +1248,7 @@ __global__ void __launch_bounds__(128, SUB ? 4 : (NB > 1 ? (CNT ? 4 : 6) : (CNT 
   CSum F[NB];
   Moments mom;
   if (__any_sync(0xffffffffu, has))
-    warp_walk<ADJ, MERGE, MOM, BG, STOP, NB, SUB, CNT>(T, P, has, i, g, ws, status, J, cnt, F,
+    warp_walk<ADJ, MERGE, MOM, BG, STOP, NB, SUB, CNT, TD>(T, P, has, i, g, ws, status, J, cnt, F,
                                                   MOM ? &mom : nullptr);
   if (MOM && has) {
 #pragma unroll
@@ -1435,6 +1448,19 @@ cudaError_t launch_walk(const TreeView& T, const long long* sink_idx, int n_sink
         walk_warp_kernel<false, true, false, false, true, 1, false, false><<<grid, 128, 0, s>>>(
             T, sink_idx, n_sink, wp, o, nullptr, status, AdjointArgs{});
     }
+    note_launch();
+    return cudaGetLastError();
+  }
+  if (wp.topdown) {  // the top-down ray walk (merged-ray walk only)
+    const SinkOut o{flux_out, counters, nullptr, nullptr, n_sink};
+    if (counters || stats)
+      walk_warp_kernel<false, true, false, false, false, 1, false, true, true>
+          <<<(n_sink + 127) / 128, 128, 0, s>>>(T, sink_idx, n_sink, wp, o, stats, status,
+                                                AdjointArgs{});
+    else
+      walk_warp_kernel<false, true, false, false, false, 1, false, false, true>
+          <<<(n_sink + 127) / 128, 128, 0, s>>>(T, sink_idx, n_sink, wp, o, nullptr, status,
+                                                AdjointArgs{});
     note_launch();
     return cudaGetLastError();
   }

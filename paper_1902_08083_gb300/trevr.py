@@ -55,7 +55,8 @@ class Params(ctypes.Structure):
                 ("bucket", ctypes.c_int), ("sinks_per_warp", ctypes.c_int),
                 ("block_size", ctypes.c_int), ("stack_depth", ctypes.c_int),
                 ("walk_variant", ctypes.c_int), ("bg_radius", ctypes.c_float),
-                ("tau_stop", ctypes.c_float), ("sub_bucket", ctypes.c_int)]
+                ("tau_stop", ctypes.c_float), ("sub_bucket", ctypes.c_int),
+                ("ray_walk", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -151,10 +152,12 @@ def _stream_ptr(stream=None):
 
 
 def make_params(theta=0.75, tau_ref=0.1, bucket=8, sinks_per_warp=0, block_size=0,
-                stack_depth=0, walk_variant=0, bg_radius=0.0, tau_stop=0.0, sub_bucket=0):
+                stack_depth=0, walk_variant=0, bg_radius=0.0, tau_stop=0.0, sub_bucket=0,
+                ray_walk=0):
+    """trevr_params; ray_walk = 1 selects the top-down ray walk (0: the paper's)."""
     return Params(float(theta), float(tau_ref), int(bucket), int(sinks_per_warp),
                   int(block_size), int(stack_depth), int(walk_variant), float(bg_radius),
-                  float(tau_stop), int(sub_bucket))
+                  float(tau_stop), int(sub_bucket), int(ray_walk))
 
 
 class Tree:
@@ -279,7 +282,8 @@ def compute_flux(tree: Tree, theta=0.75, tau_ref=0.1, sink_idx=None, out=None, c
                  stats=False, stream=None, **tuning):
     """Flux at the sinks (trevr_compute_flux). Returns flux, plus the per-sink counters
     (n, 4) int32 and/or a stats dict when asked. `tuning` holds the other fields of
-    trevr_params (launch shape, walk_variant, bg_radius, tau_stop)."""
+    trevr_params (launch shape, walk_variant, bg_radius, tau_stop, sub_bucket,
+    ray_walk)."""
     lib = tree._lib
     n = tree.n_gas if sink_idx is None else int(sink_idx.shape[0])
     if out is None:

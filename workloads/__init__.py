@@ -104,6 +104,36 @@ def clumpy(n_gas=1 << 22, n_src=1 << 14, n_clumps=16, seed=2, sigma=2.0, corr_le
                     seed=seed)
 
 
+def far_domain(n_gas=1 << 20, n_src=1024, seed=10, lo=(1000.0, 1000.0, 1000.0), side=1.0,
+               clump_frac=0.0, clump_width=3e-4, sigma=1.0, corr_len=0.05, theta=0.75,
+               tau_ref=0.1, bucket=8, n_modes=256):
+    """A domain far from the origin: gas and sources uniform in [lo, lo + side)^3 (fp32),
+    a fraction clump_frac of the gas in a Gaussian clump of the given width (in units of
+    side) at the domain's centre, a lognormal absorption field (sigma_ln = sigma, given
+    in the domain's unit coordinates) and lognormal(0, 1) luminosities."""
+    rng = np.random.default_rng(seed)
+    u = rng.random((3, n_gas))
+    m = int(clump_frac * n_gas)
+    if m:
+        u[:, :m] = np.clip(0.5 + clump_width * rng.standard_normal((3, m)), 0.0, 1.0)
+    us = rng.random((3, n_src))
+    lo32 = np.asarray(lo, np.float32)[:, None]
+    side32 = np.float32(side)
+    hi32 = (lo32 + side32).astype(np.float32)
+
+    def place(v):
+        x = (lo32 + (v * float(side32)).astype(np.float32)).astype(np.float32)
+        x = np.maximum(x, lo32)
+        return np.minimum(x, np.nextafter(hi32, np.float32(-np.inf))).astype(np.float32)
+
+    gas, src = place(u), place(us)
+    a = lognormal_alpha(rng, u.astype(np.float32), 1.0, sigma, corr_len, n_modes)
+    lum = rng.lognormal(0.0, 1.0, n_src).astype(np.float32)
+    P = _problem(f"far_{n_gas}_{n_src}", gas, a, src, lum, theta, tau_ref, bucket, seed=seed)
+    P["lo"], P["side"] = tuple(float(v) for v in lo32[:, 0]), float(side32)
+    return P
+
+
 def batched_boxes(n_boxes=64, seed=3, lo_exp=12, hi_exp=17, theta=0.75, tau_ref=0.1, bucket=8,
                   n_modes=512):
     """Independent boxes with log-uniform particle counts in [2^12, 2^17], N/64 sources
