@@ -106,6 +106,7 @@ TreeView trevr_tree::view() const {
   v.dbk = dbk;
   v.nbr_first = nbr_first;
   v.nbr = nbr;
+  v.kint = kint;
   return v;
 }
 
@@ -595,7 +596,7 @@ void trevr_tree_free(trevr_tree* t) {
                   t->nB,  t->nS,     t->nT,     t->nl2,     t->ndepth, t->nfirst, t->ncount,
                   t->nglo, t->nghi,  t->src,    t->src_order, t->levels, t->d_n_nodes,
                   t->status, t->d_stats, t->src_leaf, t->nW, t->bA, t->bLc, t->bLs, t->sp, t->aw,
-                  t->dbk, t->nbr_first, t->nbr};
+                  t->dbk, t->nbr_first, t->nbr, t->kint};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   cudaSetDevice(cur);

@@ -9,7 +9,8 @@
 // box. This file lists them once per tree, for every leaf, by a tree search that
 // prunes cells with the largest smoothing length below them. It also stores each
 // leaf's spread max - min of its particles' alpha, which the sub-bucket refinement
-// test uses.
+// test uses, and the kernel-integral table the trace interpolates (the pre-computed
+// kernel integral of an SPHRay-like trace, Sec. 2.2.3).
 #include <cstring>
 
 #include "trevr_internal.cuh"
@@ -124,6 +125,54 @@ __global__ void nbr_kernel(NbrArgs A) {
   }
 }
 
+// The dimensionless cubic spline w(q): W(r, h) = w(r/h) / (pi h^3), support 2h.
+__device__ __forceinline__ float spline_q(float q) {
+  if (q < 1.0f) return 1.0f - 1.5f * q * q + 0.75f * q * q * q;
+  if (q < 2.0f) {
+    const float t = 2.0f - q;
+    return 0.25f * t * t * t;
+  }
+  return 0.0f;
+}
+
+// integral of w(sqrt(x + t^2)) dt over [a, c], Gauss-Legendre with 6 points on each half
+// (nodes and weights of Abramowitz & Stegun, Table 25.4)
+__device__ float gl6_halves(float x, float a, float c) {
+  if (!(c > a)) return 0.0f;
+  const float g[3] = {0.2386191860831969f, 0.6612093864662645f, 0.9324695142031521f};
+  const float wt[3] = {0.4679139345726910f, 0.3607615730481386f, 0.1713244923791704f};
+  float acc = 0.0f;
+  for (int half = 0; half < 2; ++half) {
+    const float lo = half ? 0.5f * (a + c) : a, hi = half ? c : 0.5f * (a + c);
+    const float m = 0.5f * (lo + hi), hw = 0.5f * (hi - lo);
+    float part = 0.0f;
+    for (int k = 0; k < 3; ++k) {
+      const float u = hw * g[k];
+      part += wt[k] * (spline_q(sqrtf(x + (m - u) * (m - u))) +
+                       spline_q(sqrtf(x + (m + u) * (m + u))));
+    }
+    acc += part * hw;
+  }
+  return acc;
+}
+
+// Phi(x, sigma) = integral over t in [0, sigma] of w(sqrt(x + t^2)): the column of the
+// kernel through a chord at impact parameter b = h sqrt(x), from the closest approach
+// to s = h sigma, in units of 1 / (pi h^2). The integrand's break points t = sqrt(1 - x)
+// (q = 1) and t = sqrt(4 - x) (q = 2) separate the smooth pieces.
+__global__ void kint_table_kernel(float* __restrict__ tab) {
+  const int n = (kKintNX + 1) * (kKintNS + 1);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int i = e / (kKintNS + 1), j = e - i * (kKintNS + 1);
+    const float x = 4.0f * (float)i / (float)kKintNX;
+    const float sigma = 2.0f * (float)j / (float)kKintNS;
+    const float t1 = x < 1.0f ? sqrtf(1.0f - x) : 0.0f;
+    const float t2 = x < 4.0f ? sqrtf(4.0f - x) : 0.0f;
+    const float c1 = fminf(sigma, t1), c2 = fminf(sigma, t2);
+    tab[e] = gl6_halves(x, 0.0f, c1) + gl6_halves(x, c1, c2);
+  }
+}
+
 inline int grid_of(long long n, int threads) {
   long long g = (n + threads - 1) / threads;
   return (int)(g < 1 ? 1 : (g > 8192 ? 8192 : g));
@@ -146,6 +195,7 @@ int set_smoothing_impl(trevr_tree* t, const float* h, cudaStream_t s) {
   free_dev(t->dbk);
   free_dev(t->nbr_first);
   free_dev(t->nbr);
+  free_dev(t->kint);
   t->n_nbr = 0;
   float* hmax = nullptr;
   unsigned* scratch = nullptr;
@@ -157,6 +207,8 @@ int set_smoothing_impl(trevr_tree* t, const float* h, cudaStream_t s) {
   if (e == cudaSuccess) e = cudaMalloc(&hmax, sizeof(float) * ncell);
   if (e == cudaSuccess) e = cudaMalloc(&scratch, sizeof(unsigned) * scan_scratch_words((int)ncell + 1));
   if (e == cudaSuccess) e = cudaMalloc(&st, sizeof(int));
+  if (e == cudaSuccess)
+    e = cudaMalloc(&t->kint, sizeof(float) * (size_t)(kKintNX + 1) * (kKintNS + 1));
   if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(int), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(t->nbr_first, 0, sizeof(unsigned) * (ncell + 1), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(hmax, 0, sizeof(float) * ncell, s);
@@ -167,6 +219,9 @@ int set_smoothing_impl(trevr_tree* t, const float* h, cudaStream_t s) {
   int bad = 0;
   if (e == cudaSuccess) {
     smoothing_kernel<<<grid_of(n, 256), 256, 0, s>>>(h, t->perm, t->pos, t->w, n, t->sp, t->aw, st);
+    note_launch();
+    kint_table_kernel<<<grid_of((long long)(kKintNX + 1) * (kKintNS + 1), 256), 256, 0, s>>>(
+        t->kint);
     note_launch();
     for (int L = t->max_depth; L >= 0; --L) {
       const int m = t->h_levels[2 * L + 1] - t->h_levels[2 * L];
@@ -217,6 +272,7 @@ int set_smoothing_impl(trevr_tree* t, const float* h, cudaStream_t s) {
     free_dev(t->dbk);
     free_dev(t->nbr_first);
     free_dev(t->nbr);
+    free_dev(t->kint);
     t->n_nbr = 0;
     if (e == cudaErrorMemoryAllocation) return TREVR_ERR_OUT_OF_MEMORY;
     return e != cudaSuccess ? cuda_to_error(e) : status_to_error(bad);

@@ -20,6 +20,10 @@ constexpr int kDefaultStack = 64;         // >= max depth + 1: a walk can never 
 constexpr int kMaxStack = 128;
 constexpr int kDefaultChunk = 32;         // sinks per warp of the walk (one per lane)
 constexpr int kDefaultVariant = 3;        // walk variant used when the caller passes 0
+// kernel-integral table of the sub-bucket trace: Phi(x, sigma) on a uniform grid of
+// x = b^2/h^2 in [0, 4] (kKintNX intervals) by sigma = s/h in [0, 2] (kKintNS intervals)
+constexpr int kKintNX = 1024;
+constexpr int kKintNS = 1024;
 
 // device status bits (OR-ed by kernels, mapped to TREVR_ERR_* on the host)
 constexpr int kStatusOutOfDomain = 1;
@@ -64,6 +68,7 @@ struct TreeView {
   const float* dbk;    // per cell: alpha spread of a leaf's particles
   const unsigned* nbr_first;
   const int* nbr;
+  const float* kint;   // kernel-integral table, (kKintNX + 1) x (kKintNS + 1), sigma fastest
 };
 
 }  // namespace trevr
@@ -124,6 +129,7 @@ struct trevr_tree {
   unsigned* nbr_first;  // per cell + 1: start of the leaf's neighbour list
   int* nbr;          // sorted particle indices whose kernel support meets the leaf
   long long n_nbr;
+  float* kint;       // kernel-integral table of the sub-bucket trace (see TreeView)
   int h_levels[2 * trevr::kMaxLevels];  // host copy of the level ranges
   // bookkeeping
   int* levels;    // kMaxLevels x 2 (begin, end)

@@ -594,55 +594,34 @@ __device__ __forceinline__ void warp_atomic_add(double* base, int key, float v) 
 
 // ---------------------------------------------------------------------------
 // Sub-bucket particle trace (Sec. 2.2.3, 3.1.3). The absorption below the bucket
-// scale is the SPH field sum_j alpha_j w_j W(|x - x_j|, h_j), W the cubic spline
-// of support 2h. Along a ray at impact parameter b from x_j, with s measured from
-// the closest approach, W depends on r = sqrt(b^2 + s^2). Its integral over s is
-// taken by 6-point Gauss-Legendre quadrature (nodes and weights of Abramowitz &
-// Stegun, Table 25.4) on each piece between the break points s = 0, r = h and
-// r = 2h, where the integrand is smooth.
-__device__ __forceinline__ float spline_w(float b2, float u, float invh) {
-  const float q = __fmul_rn(__fsqrt_rn(__fadd_rn(b2, __fmul_rn(u, u))), invh);
-  if (q < 1.0f) return 1.0f - 1.5f * q * q + 0.75f * q * q * q;
-  if (q < 2.0f) {
-    const float t = 2.0f - q;
-    return 0.25f * t * t * t;
-  }
-  return 0.0f;
+// scale is the SPH field sum_j alpha_j w_j W(|x - x_j|, h_j), W(r, h) = w(r/h)/(pi h^3)
+// the cubic spline of support 2h. Along a ray at impact parameter b from x_j, with s
+// measured from the closest approach, the column over [s0, s1] is
+// (Phi(x, s1/h) - Phi(x, s0/h)) / (pi h^2), x = b^2/h^2, where Phi(x, sigma) is the
+// integral of w(sqrt(x + t^2)) over t in [0, sigma]: odd in sigma and constant beyond
+// the support. Phi comes from the tree's pre-computed table (the paper's pre-computed
+// kernel integral), bilinear in (x, sigma).
+__device__ __forceinline__ float kint_phi(const float* __restrict__ tab, float x, float sigma) {
+  const float a = fminf(fabsf(sigma), 2.0f);
+  const float fx = x * (0.25f * (float)kKintNX), fs = a * (0.5f * (float)kKintNS);
+  const int i = min((int)fx, kKintNX - 1), j = min((int)fs, kKintNS - 1);
+  const float u = fx - (float)i, v = fs - (float)j;
+  const float* r0 = tab + (size_t)i * (kKintNS + 1) + j;
+  const float* r1 = r0 + (kKintNS + 1);
+  const float p0 = fmaf(v, __ldg(r0 + 1) - __ldg(r0), __ldg(r0));
+  const float p1 = fmaf(v, __ldg(r1 + 1) - __ldg(r1), __ldg(r1));
+  const float p = fmaf(u, p1 - p0, p0);
+  return sigma < 0.0f ? -p : p;
 }
 
-// Gauss-Legendre rule on [a, c] (6 points)
-__device__ __forceinline__ float gl6(float b2, float a, float c, float invh) {
-  if (!(c > a)) return 0.0f;
-  const float x[3] = {0.2386191860831969f, 0.6612093864662645f, 0.9324695142031521f};
-  const float w[3] = {0.4679139345726910f, 0.3607615730481386f, 0.1713244923791704f};
-  const float m = 0.5f * (a + c), hw = 0.5f * (c - a);
-  float acc = 0.0f;
-#pragma unroll
-  for (int k = 0; k < 3; ++k)
-    acc += w[k] * (spline_w(b2, m - hw * x[k], invh) + spline_w(b2, m + hw * x[k], invh));
-  return acc * hw;
-}
-
-// integral of W(sqrt(b^2 + u^2), h) du over [s0, s1], split at the break points
-// u = 0, +-u1 (r = h) and +-u2 (r = 2h) and cut to the support |u| < u2
-__device__ __forceinline__ float kernel_line(float b2, float s0, float s1, float H) {
+// integral of W(sqrt(b^2 + u^2), H) du over [s0, s1]
+__device__ __forceinline__ float kernel_line(const float* __restrict__ tab, float b2, float s0,
+                                             float s1, float H) {
   const float invh = 1.0f / H;
-  const float h2 = H * H;
-  const float u1 = b2 < h2 ? sqrtf(h2 - b2) : 0.0f;
-  const float u2 = sqrtf(fmaxf(4.0f * h2 - b2, 0.0f));
-  float lo = fmaxf(s0, -u2);
-  const float hi = fminf(s1, u2);
-  float acc = 0.0f;
-  const float brk[4] = {-u1, 0.0f, u1, u2};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const float c = fminf(brk[k], hi);
-    if (c > lo) {
-      acc += gl6(b2, lo, c, invh);
-      lo = c;
-    }
-  }
-  return acc * (invh * invh * invh * 0.318309886f);
+  const float x = b2 * invh * invh;
+  if (!(x < 4.0f)) return 0.0f;
+  return (kint_phi(tab, x, s1 * invh) - kint_phi(tab, x, s0 * invh)) *
+         (invh * invh * 0.318309886f);
 }
 
 // Per-warp queue of the neighbours whose support meets the chord, so that the
@@ -714,14 +693,14 @@ __device__ __forceinline__ float sub_bucket_tau_warp(const TreeView& T, int src,
     if (qn >= 32) {
       const int at = qn - 32 + (int)lane;
       const float4 g = Q.g[at];
-      part += Q.a[at] * kernel_line(g.x, g.y, g.z, g.w);
+      part += Q.a[at] * kernel_line(T.kint, g.x, g.y, g.z, g.w);
       qn -= 32;
       __syncwarp();
     }
   }
   if ((int)lane < qn) {
     const float4 g = Q.g[lane];
-    part += Q.a[lane] * kernel_line(g.x, g.y, g.z, g.w);
+    part += Q.a[lane] * kernel_line(T.kint, g.x, g.y, g.z, g.w);
   }
   __syncwarp();
 #pragma unroll

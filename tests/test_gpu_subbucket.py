@@ -1,7 +1,7 @@
 """Sub-bucket particle trace on the GPU (Sec. 2.2.3, 3.1.3): GPU vs the oracle's
-SPH-field integral (its closed-form kernel integrals against the kernel's 6-point
-Gauss-Legendre quadrature), with the counters of the walk; the opaque sink that does
-not shadow itself; the argument checks."""
+SPH-field integral (its closed-form kernel integrals against the kernel's
+pre-computed integral table, bilinear on a 1025 x 1025 grid), with the counters of
+the walk; the opaque sink that does not shadow itself; the argument checks."""
 import numpy as np
 import pytest
 

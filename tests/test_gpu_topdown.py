@@ -50,13 +50,16 @@ def test_topdown_lognormal_matches_oracle(theta, tau_ref):
 
 
 def test_topdown_full_refinement_equals_bottom_up():
-    # at tau_ref = 0 both walks sum the same leaves (in another order)
+    # at tau_ref = 0 both walks sum the same leaves (in another order): the same
+    # interactions, segments and visited cells; the refinement counts differ, since
+    # the top-down walk splits every cell below A while the bottom-up walk lists the
+    # cells along the two paths without splitting them
     from paper_1902_08083_gb300 import trevr
     P = _lognormal(workloads.uniform_box(n_gas=20000, n_src=100, seed=23))
     G = gpu_tree(P)
     f_td, c_td, _ = _run(G, 0.75, 0.0)
     f_bu, c_bu = trevr.compute_flux(G, 0.75, 0.0, counters=True)
-    np.testing.assert_array_equal(c_td, c_bu.cpu().numpy())
+    np.testing.assert_array_equal(c_td[:, :3], c_bu.cpu().numpy()[:, :3])
     np.testing.assert_allclose(f_td, f_bu.cpu().numpy(), rtol=2e-6)
 
 
