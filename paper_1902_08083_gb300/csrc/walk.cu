@@ -97,6 +97,15 @@ __device__ __forceinline__ void slab(float lo, float hi, float p, float d, float
   }
 }
 
+// the slab of an axis the ray moves along (d != 0): the same steps as slab()
+__device__ __forceinline__ void slab_nz(float lo, float hi, float p, float inv, float& t0,
+                                        float& t1) {
+  const float ta = __fmul_rn(__fsub_rn(lo, p), inv);
+  const float tb = __fmul_rn(__fsub_rn(hi, p), inv);
+  t0 = fmaxf(t0, fminf(ta, tb));
+  t1 = fminf(t1, fmaxf(ta, tb));
+}
+
 // gradient-carrying slab: remembers which axis sets t0 / t1
 __device__ __forceinline__ void slab_g(int k, float lo, float hi, float p, float d, float inv,
                                        float& t0, float& t1, int& k0, int& k1, bool& miss) {
@@ -769,6 +778,7 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
     }
   }
   const bool traced = active;
+  const bool nz = dx != 0.0f && dy != 0.0f && dz != 0.0f;  // the ray moves along every axis
   KSum tau;
   KSum taub[NB];  // (NB > 1) optical depth of each band
   bool cut = false;
@@ -867,10 +877,10 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
           else box = S;
           ++b;
         }
-        if (++boxes > box_limit) {
-          atomicOr(status, kStatusIterationLimit);
-          active = false;
-        } else {
+        // Each iteration clips one base segment or one child of a pushed pair, and the
+        // pushes are capped by box_limit below, so a ray ends after at most
+        // nb + 2 box_limit iterations (the walk's hang guard).
+        {
           const float4 a = __ldg(&T.nA[box]);
           const float4 bb = __ldg(&T.nB[box]);
           const bool want_grad = ADJ && pass == 1 && src_j < 0;
@@ -881,6 +891,10 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
             slab_g(0, a.x, bb.x, px, dx, ix, t0, t1, k0, k1, miss);
             slab_g(1, a.y, bb.y, py, dy, iy, t0, t1, k0, k1, miss);
             slab_g(2, a.z, bb.z, pz, dz, iz, t0, t1, k0, k1, miss);
+          } else if (nz) {  // no axis along which the ray stays still: no face tests
+            slab_nz(a.x, bb.x, px, ix, t0, t1);
+            slab_nz(a.y, bb.y, py, iy, t0, t1);
+            slab_nz(a.z, bb.z, pz, iz, t0, t1);
           } else {
             slab(a.x, bb.x, px, dx, ix, t0, t1, miss);
             slab(a.y, bb.y, py, dy, iy, t0, t1, miss);
@@ -895,6 +909,9 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
               if (child >= 0) {
                 if (rsp + 1 > kRayStack) {
                   atomicOr(status, kStatusStackOverflow);
+                  active = false;
+                } else if (++boxes > box_limit) {
+                  atomicOr(status, kStatusIterationLimit);
                   active = false;
                 } else {
                   if (CNT) ++cnt.ref;
