@@ -70,7 +70,10 @@ struct NbrArgs {
   float pad;         // absolute slack added to every support radius
   unsigned* count;   // count pass: per cell
   const unsigned* first;  // fill pass: per cell start
-  int* nbr;               // fill pass: output
+  int* nbr;               // fill pass: output (sorted particle index)
+  const float* aw;        // per sorted particle alpha * w
+  float4* nbr_sp;         // fill pass: output, the entry's (x, y, z, h)
+  float* nbr_aw;          // fill pass: output, the entry's alpha * w
   int* status;
 };
 
@@ -116,7 +119,12 @@ __global__ void nbr_kernel(NbrArgs A) {
         const float ez = fmaxf(fmaxf(__fsub_rn(lo.z, q.z), __fsub_rn(q.z, hi.z)), 0.0f);
         const float r = fmaf(2.0f * q.w, 1.00001f, A.pad);
         if (ex * ex + ey * ey + ez * ez < r * r) {
-          if (FILL && out < out_end) A.nbr[out++] = i;
+          if (FILL && out < out_end) {
+            A.nbr[out] = i;
+            A.nbr_sp[out] = q;
+            A.nbr_aw[out] = A.aw[i];
+            ++out;
+          }
           ++c;
         }
       }
@@ -195,6 +203,8 @@ int set_smoothing_impl(trevr_tree* t, const float* h, cudaStream_t s) {
   free_dev(t->dbk);
   free_dev(t->nbr_first);
   free_dev(t->nbr);
+  free_dev(t->nbr_sp);
+  free_dev(t->nbr_aw);
   free_dev(t->kint);
   t->n_nbr = 0;
   float* hmax = nullptr;
@@ -251,10 +261,16 @@ int set_smoothing_impl(trevr_tree* t, const float* h, cudaStream_t s) {
     if (total > 0x7fffffffu) {
       e = cudaErrorMemoryAllocation;
     } else {
-      e = cudaMalloc(&t->nbr, sizeof(int) * (total > 0 ? total : 1));
+      const size_t m = total > 0 ? total : 1;
+      e = cudaMalloc(&t->nbr, sizeof(int) * m);
+      if (e == cudaSuccess) e = cudaMalloc(&t->nbr_sp, sizeof(float4) * m);
+      if (e == cudaSuccess) e = cudaMalloc(&t->nbr_aw, sizeof(float) * m);
       if (e == cudaSuccess) {
         A.first = t->nbr_first;
         A.nbr = t->nbr;
+        A.aw = t->aw;
+        A.nbr_sp = t->nbr_sp;
+        A.nbr_aw = t->nbr_aw;
         nbr_kernel<true><<<grid_of((long long)ncell, 128), 128, 0, s>>>(A);
         note_launch();
         cudaMemcpyAsync(&bad, st, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -272,6 +288,8 @@ int set_smoothing_impl(trevr_tree* t, const float* h, cudaStream_t s) {
     free_dev(t->dbk);
     free_dev(t->nbr_first);
     free_dev(t->nbr);
+    free_dev(t->nbr_sp);
+    free_dev(t->nbr_aw);
     free_dev(t->kint);
     t->n_nbr = 0;
     if (e == cudaErrorMemoryAllocation) return TREVR_ERR_OUT_OF_MEMORY;

@@ -68,6 +68,8 @@ struct TreeView {
   const float* dbk;    // per cell: alpha spread of a leaf's particles
   const unsigned* nbr_first;
   const int* nbr;
+  const float4* nbr_sp;  // per list entry: the neighbour's (x, y, z, h), contiguous per leaf
+  const float* nbr_aw;   // per list entry: the neighbour's alpha * w
   const float* kint;   // kernel-integral table, (kKintNX + 1) x (kKintNS + 1), sigma fastest
 };
 
@@ -128,6 +130,8 @@ struct trevr_tree {
   float* dbk;        // per cell: max - min of alpha over a leaf's particles (0 inside)
   unsigned* nbr_first;  // per cell + 1: start of the leaf's neighbour list
   int* nbr;          // sorted particle indices whose kernel support meets the leaf
+  float4* nbr_sp;    // the same entries' (x, y, z, h), so a leaf's list is read coalesced
+  float* nbr_aw;     // the same entries' alpha * w
   long long n_nbr;
   float* kint;       // kernel-integral table of the sub-bucket trace (see TreeView)
   int h_levels[2 * trevr::kMaxLevels];  // host copy of the level ranges

@@ -106,6 +106,15 @@ __device__ __forceinline__ void slab_nz(float lo, float hi, float p, float inv, 
   t1 = fminf(t1, fmaxf(ta, tb));
 }
 
+__device__ __forceinline__ void slab_g_nz(int k, float lo, float hi, float p, float inv,
+                                          float& t0, float& t1, int& k0, int& k1) {
+  const float ta = __fmul_rn(__fsub_rn(lo, p), inv);
+  const float tb = __fmul_rn(__fsub_rn(hi, p), inv);
+  const float tn = fminf(ta, tb), tx = fmaxf(ta, tb);
+  if (tn > t0) { t0 = tn; k0 = k; }
+  if (tx < t1) { t1 = tx; k1 = k; }
+}
+
 // gradient-carrying slab: remembers which axis sets t0 / t1
 __device__ __forceinline__ void slab_g(int k, float lo, float hi, float p, float d, float inv,
                                        float& t0, float& t1, int& k0, int& k1, bool& miss) {
@@ -674,9 +683,9 @@ __device__ __forceinline__ float sub_bucket_tau_warp(const TreeView& T, int src,
     float a = 0.0f, b2 = 0.0f, sa = 0.0f, sb = 0.0f, H = 1.0f;
     if (k < k1) {
       const int j = __ldg(&T.nbr[k]);
-      a = __ldg(&T.aw[j]);
+      a = __ldg(&T.nbr_aw[k]);
       if (j != si && a > 0.0f) {
-        const float4 q = __ldg(&T.sp[j]);
+        const float4 q = __ldg(&T.nbr_sp[k]);
         const float ux = q.x - px, uy = q.y - py, uz = q.z - pz;
         const float tc = (ux * dx + uy * dy + uz * dz) / s2;
         const float ex = ux - tc * dx, ey = uy - tc * dy, ez = uz - tc * dz;
@@ -887,7 +896,11 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
           float t0 = 0.0f, t1 = 1.0f;
           bool miss = false;
           int k0 = -1, k1 = -1;
-          if (want_grad) {
+          if (want_grad && nz) {
+            slab_g_nz(0, a.x, bb.x, px, ix, t0, t1, k0, k1);
+            slab_g_nz(1, a.y, bb.y, py, iy, t0, t1, k0, k1);
+            slab_g_nz(2, a.z, bb.z, pz, iz, t0, t1, k0, k1);
+          } else if (want_grad) {
             slab_g(0, a.x, bb.x, px, dx, ix, t0, t1, k0, k1, miss);
             slab_g(1, a.y, bb.y, py, dy, iy, t0, t1, k0, k1, miss);
             slab_g(2, a.z, bb.z, pz, dz, iz, t0, t1, k0, k1, miss);
@@ -1214,14 +1227,15 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
 // 8 blocks of 128 per SM (at most 64 registers): measured 4% faster forward and 8%
 // faster adjoint than the compiler's own 70 registers at 7 blocks. Without
 // counters (CNT = false, the plain flux when the caller asks for no counters or
-// stats) the walk fits 9 blocks (56 registers): 5% faster again on the clumpy
-// workload (135 ms against 142.8 ms); 10 blocks spilled more and were slower.
+// stats) the walk runs 12 blocks (40 registers, spilling to L1): 2.7% faster than
+// 9 blocks (56 registers) on the clumpy workload, 119.8 against 123.2 ms; 10
+// blocks were slower (141 ms).
 // CNT = false keeps no per-sink counters; the fluxes are bit-identical. The band
 // walks without counters fit 6 blocks (74 registers, no spills) instead of 4:
 // 245 ms against 262 ms for four bands on the clumpy workload.
 template <bool ADJ, bool MERGE, bool MOM = false, bool BG = false, bool STOP = false, int NB = 1,
           bool SUB = false, bool CNT = true, bool TD = false>
-__global__ void __launch_bounds__(128, SUB ? 4 : (NB > 1 ? (CNT ? 4 : 6) : (CNT ? 8 : 9))) walk_warp_kernel(TreeView T, const long long* sink_idx,
+__global__ void __launch_bounds__(128, SUB ? 4 : (NB > 1 ? (CNT ? 4 : 6) : (CNT ? 8 : 12))) walk_warp_kernel(TreeView T, const long long* sink_idx,
                                                         int n_sink, WalkParams P, SinkOut out,
                                                         unsigned long long* stats, int* status,
                                                         AdjointArgs J) {
