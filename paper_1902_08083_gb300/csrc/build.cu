@@ -2,9 +2,11 @@
 // Morton keys -> stable radix sort -> top-down binary tree of Morton prefixes,
 // level by level -> source deposit -> bottom-up cell moments, level by level.
 //
-// Every kernel is launched with a fixed grid and reads the extent of its level
-// from device memory, so the whole topology pass runs without host round trips;
-// the host synchronises once, after the topology, to size the moment pass.
+// The topology pass is one cooperative launch that walks the levels with grid-wide
+// barriers (or, where that is not possible, a pair of fixed-grid launches per level
+// that read the extent of their level from device memory), so it runs without host
+// round trips; the host synchronises once, after the topology, to size the moment pass.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -259,10 +261,12 @@ __global__ void topo_init_kernel(TopoArrays A, int n) {
   }
 }
 
+// Values that other blocks wrote earlier in the same launch (the one-launch topology
+// below) are read through L2 (ld.global.cg): L1 is not coherent across SMs.
 __device__ __forceinline__ void level_chunk(const int* levels, int L, int* begin, int* end,
                                             int* c0, int* c1) {
-  *begin = levels[2 * L];
-  *end = levels[2 * L + 1];
+  *begin = __ldcg(&levels[2 * L]);
+  *end = __ldcg(&levels[2 * L + 1]);
   int m = *end - *begin;
   int chunk = (m + gridDim.x - 1) / gridDim.x;
   *c0 = *begin + blockIdx.x * chunk;
@@ -270,13 +274,13 @@ __device__ __forceinline__ void level_chunk(const int* levels, int L, int* begin
 }
 
 // Decide leaf / split for every cell of level L; count internal cells per block.
-__global__ void __launch_bounds__(kTopoThreads) topo_split_kernel(TopoArrays A, int L) {
+__device__ __forceinline__ void topo_split_level(const TopoArrays& A, int L) {
   __shared__ unsigned long long red[32];
   int begin, end, c0, c1;
   level_chunk(A.levels, L, &begin, &end, &c0, &c1);
   unsigned long long cnt = 0;
   for (int X = c0 + threadIdx.x; X < c1; X += blockDim.x) {
-    const int f = A.nfirst[X], c = A.ncount[X];
+    const int f = __ldcg(&A.nfirst[X]), c = __ldcg(&A.ncount[X]);
     const unsigned long long kf = A.key[f], kl = A.key[f + c - 1];
     if (c <= A.bucket || kf == kl) {
       A.nsplit[X] = -1;
@@ -303,7 +307,7 @@ __global__ void __launch_bounds__(kTopoThreads) topo_split_kernel(TopoArrays A, 
 
 // Allocate the children of the internal cells of level L (in cell order, two
 // consecutive slots each) and write their ranges and boxes.
-__global__ void __launch_bounds__(kTopoThreads) topo_emit_kernel(TopoArrays A, int L) {
+__device__ __forceinline__ void topo_emit_level(const TopoArrays& A, int L) {
   __shared__ unsigned scan_smem[32];
   __shared__ unsigned long long red[32];
   int begin, end, c0, c1;
@@ -311,7 +315,7 @@ __global__ void __launch_bounds__(kTopoThreads) topo_emit_kernel(TopoArrays A, i
   // offset of this block = sum of the counts of the blocks before it
   unsigned long long pre = 0, all = 0;
   for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-    unsigned v = A.bcount[b];
+    unsigned v = __ldcg(&A.bcount[b]);
     all += v;
     if (b < (int)blockIdx.x) pre += v;
   }
@@ -334,12 +338,13 @@ __global__ void __launch_bounds__(kTopoThreads) topo_emit_kernel(TopoArrays A, i
     unsigned off = block_exclusive_scan(internal ? 1u : 0u, scan_smem, &total);
     if (internal) {
       const int child = end + 2 * (int)(running + off);
-      const int f = A.nfirst[X], c = A.ncount[X], k = A.nsplit[X], b = A.nbit[X];
+      const int f = __ldcg(&A.nfirst[X]), c = __ldcg(&A.ncount[X]), k = A.nsplit[X],
+                b = A.nbit[X];
       const int axis = (62 - b) % 3;
       const int shift = kGridBits - 1 - (62 - b) / 3;
       const unsigned g = key_coord(A.key[f], axis);
       const int plane = (int)(((g >> shift) | 1u) << shift);
-      int4 lo = A.nglo[X], hi = A.nghi[X];
+      int4 lo = __ldcg(&A.nglo[X]), hi = __ldcg(&A.nghi[X]);
       A.nT[X].x = child;
       A.nglo[X].w = axis;
       int4 lo1 = make_int4(lo.x, lo.y, lo.z, 0), hi1 = make_int4(hi.x, hi.y, hi.z, 0);
@@ -361,6 +366,29 @@ __global__ void __launch_bounds__(kTopoThreads) topo_emit_kernel(TopoArrays A, i
       A.ndepth[child + 1] = L + 1;
     }
     running += total;
+  }
+}
+
+__global__ void __launch_bounds__(kTopoThreads) topo_split_kernel(TopoArrays A, int L) {
+  topo_split_level(A, L);
+}
+
+__global__ void __launch_bounds__(kTopoThreads) topo_emit_kernel(TopoArrays A, int L) {
+  topo_emit_level(A, L);
+}
+
+// Every level in one cooperative launch: split, grid-wide barrier, emit, barrier, until
+// a level has no cells (every block reads the same level extent after a barrier, so
+// all leave the loop together). The per-level pair of launches is the fallback when
+// a cooperative launch is not possible.
+__global__ void __launch_bounds__(kTopoThreads) topo_levels_kernel(TopoArrays A) {
+  cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+  for (int L = 0; L < kMaxLevels - 1; ++L) {
+    if (__ldcg(&A.levels[2 * L + 1]) <= __ldcg(&A.levels[2 * L])) break;
+    topo_split_level(A, L);
+    grid.sync();
+    topo_emit_level(A, L);
+    grid.sync();
   }
 }
 
@@ -467,10 +495,24 @@ struct MomentArrays {
 // a grid plane relative to the domain's lower corner: g * h, rounded once
 __device__ __forceinline__ float rel_plane(float h, int g) { return __fmul_rn((float)g, h); }
 
-__global__ void moments_level_kernel(MomentArrays A, int L) {
-  const int begin = A.levels[2 * L], end = A.levels[2 * L + 1];
-  for (int X = begin + blockIdx.x * blockDim.x + threadIdx.x; X < end;
-       X += gridDim.x * blockDim.x) {
+// a child's moments, written by another block earlier in the same launch: through L2
+__device__ __forceinline__ Moments load_moments(const Moments* p) {
+  Moments m;
+  m.W = __ldcg(&p->W);
+  m.WA = __ldcg(&p->WA);
+  m.L = __ldcg(&p->L);
+  for (int d = 0; d < 3; ++d) {
+    m.LY[d] = __ldcg(&p->LY[d]);
+    m.amin[d] = __ldcg(&p->amin[d]);
+    m.amax[d] = __ldcg(&p->amax[d]);
+  }
+  return m;
+}
+
+// the moments and the walk records of one cell, from its particles and sources (a
+// leaf) or from its two children (whose moments are complete)
+__device__ __forceinline__ void moments_cell(const MomentArrays& A, int X) {
+  {
     const int4 t = A.nT[X];
     Moments m;
     if (t.x < 0) {
@@ -499,8 +541,8 @@ __global__ void moments_level_kernel(MomentArrays A, int L) {
       const double ab = __ddiv_rn(swa, sw);
       for (int d = 0; d < 3; ++d) m.amin[d] = m.amax[d] = ab;
     } else {
-      const Moments& m1 = A.mom[t.x];
-      const Moments& m2 = A.mom[t.x + 1];
+      const Moments m1 = load_moments(&A.mom[t.x]);
+      const Moments m2 = load_moments(&A.mom[t.x + 1]);
       m.W = __dadd_rn(m1.W, m2.W);
       m.WA = __dadd_rn(m1.WA, m2.WA);
       m.L = __dadd_rn(m1.L, m2.L);
@@ -550,10 +592,78 @@ __global__ void moments_level_kernel(MomentArrays A, int L) {
   }
 }
 
+__global__ void moments_level_kernel(MomentArrays A, int L) {
+  const int begin = A.levels[2 * L], end = A.levels[2 * L + 1];
+  for (int X = begin + blockIdx.x * blockDim.x + threadIdx.x; X < end;
+       X += gridDim.x * blockDim.x)
+    moments_cell(A, X);
+}
+
+// Every level, deepest first, in one cooperative launch with a grid-wide barrier
+// between levels (the per-level launches are the fallback).
+__global__ void moments_levels_kernel(MomentArrays A, int max_depth) {
+  cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+  for (int L = max_depth; L >= 0; --L) {
+    const int begin = A.levels[2 * L], end = A.levels[2 * L + 1];
+    for (int X = begin + blockIdx.x * blockDim.x + threadIdx.x; X < end;
+         X += gridDim.x * blockDim.x)
+      moments_cell(A, X);
+    grid.sync();
+  }
+}
+
 // ------------------------------------------------------------------------------------
 // Host driver
 // ------------------------------------------------------------------------------------
 namespace {
+
+// One cooperative launch of the whole topology pass, with as many blocks (at most
+// kTopoBlocks, the size of the per-block count array) as can be resident together.
+// Returns false, leaving no error behind, when the device cannot run it.
+bool launch_topology_cooperative(TopoArrays& TA, cudaStream_t s) {
+  int dev = 0, coop = 0, n_sm = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, topo_levels_kernel, kTopoThreads,
+                                                    0) != cudaSuccess ||
+      !coop || per_sm < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  const int grid = per_sm * n_sm < kTopoBlocks ? per_sm * n_sm : kTopoBlocks;
+  void* args[] = {&TA};
+  if (cudaLaunchCooperativeKernel((void*)topo_levels_kernel, dim3(grid), dim3(kTopoThreads), args,
+                                  0, s) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  note_launch();
+  return true;
+}
+
+// The bottom-up moment pass in one cooperative launch (as many blocks of 128 as can be
+// resident together). Returns false, leaving no error behind, when it cannot run.
+bool launch_moments_cooperative(MomentArrays& MA, int max_depth, cudaStream_t s) {
+  int dev = 0, coop = 0, n_sm = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, moments_levels_kernel, 128, 0) !=
+          cudaSuccess ||
+      !coop || per_sm < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  void* args[] = {&MA, &max_depth};
+  if (cudaLaunchCooperativeKernel((void*)moments_levels_kernel, dim3(per_sm * n_sm), dim3(128),
+                                  args, 0, s) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  note_launch();
+  return true;
+}
 
 struct Allocs {
   std::vector<void*> ptrs;
@@ -695,11 +805,13 @@ int build_tree_impl(const float* gas_xyz, const float* alpha, const float* weigh
   TA.bucket = bucket;
   topo_init_kernel<<<1, 128, 0, s>>>(TA, n);
   note_launch();
-  for (int L = 0; L < kMaxLevels - 1; ++L) {
-    topo_split_kernel<<<kTopoBlocks, kTopoThreads, 0, s>>>(TA, L);
-    note_launch();
-    topo_emit_kernel<<<kTopoBlocks, kTopoThreads, 0, s>>>(TA, L);
-    note_launch();
+  if (!launch_topology_cooperative(TA, s)) {
+    for (int L = 0; L < kMaxLevels - 1; ++L) {
+      topo_split_kernel<<<kTopoBlocks, kTopoThreads, 0, s>>>(TA, L);
+      note_launch();
+      topo_emit_kernel<<<kTopoBlocks, kTopoThreads, 0, s>>>(TA, L);
+      note_launch();
+    }
   }
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return fail(cuda_to_error(err));
@@ -764,12 +876,14 @@ int build_tree_impl(const float* gas_xyz, const float* alpha, const float* weigh
   MA.nS = t->nS;
   MA.nl2 = t->nl2;
   MA.h = t->h;
-  for (int L = max_depth; L >= 0; --L) {
-    int m = levels[2 * L + 1] - levels[2 * L];
-    int blocks = grid_for(m, 128);
-    if (blocks > 4096) blocks = 4096;
-    moments_level_kernel<<<blocks, 128, 0, s>>>(MA, L);
-    note_launch();
+  if (!launch_moments_cooperative(MA, max_depth, s)) {
+    for (int L = max_depth; L >= 0; --L) {
+      int m = levels[2 * L + 1] - levels[2 * L];
+      int blocks = grid_for(m, 128);
+      if (blocks > 4096) blocks = 4096;
+      moments_level_kernel<<<blocks, 128, 0, s>>>(MA, L);
+      note_launch();
+    }
   }
   cudaMemcpyAsync(t->d_n_nodes, &levels[2 * max_depth + 1], sizeof(int), cudaMemcpyHostToDevice, s);
   tmp.release();

@@ -879,11 +879,14 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
             slot = box + 1;
           }
         } else {
-          if (nb == 1) box = base1;
-          else if (b == 0) box = C;
-          else if (b <= nCs) box = path[dC - b + 1] ^ 1;
-          else if (b <= nCs + nSs) box = anc[dstar + 1 + (b - nCs)] ^ 1;
-          else box = S;
+          if (nb == 1) {
+            box = base1;
+          } else if (b <= nCs) {  // C = path[dC], then the siblings up C's path
+            box = path[dC - max(b - 1, 0)] ^ (b > 0 ? 1 : 0);
+          } else {  // the siblings down S's path, then S = anc[dS]
+            const int j = b - nCs;
+            box = anc[dstar + 1 + min(j, nSs)] ^ (j <= nSs ? 1 : 0);
+          }
           ++b;
         }
         // Each iteration clips one base segment or one child of a pushed pair, and the
@@ -1285,10 +1288,11 @@ __global__ void __launch_bounds__(128, SUB ? 4 : (NB > 1 ? (CNT ? 4 : 6) : (CNT 
 
 // Batched form of the warp-shared walk: each work item is cut into groups of 32
 // consecutive sinks, one warp walk per group.
-// CNT = false (no stats asked for): no counters, and 9 blocks-of-128 worth of
-// threads per SM instead of 8, as for the single-tree walk.
+// CNT = false (no stats asked for): no counters, and 12 blocks-of-128 worth of
+// threads per SM instead of 8, as for the single-tree walk (2.8% faster than 9 on
+// the 64 boxes).
 template <int BS, bool MERGE, bool CNT = true>
-__global__ void __launch_bounds__(BS, CNT ? 1024 / BS : 1152 / BS) walk_warp_batched_kernel(
+__global__ void __launch_bounds__(BS, CNT ? 1024 / BS : 1536 / BS) walk_warp_batched_kernel(
     const TreeView* __restrict__ views, float* const* __restrict__ flux_out,
     const int2* __restrict__ items, int n_items, int item, unsigned* counter, WalkParams P,
     unsigned long long* stats, int* status) {
