@@ -1022,225 +1022,6 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
   }
 }
 
-// Queued rays (QK > 0 in warp_walk; the flux and its options, not the adjoint). A
-// lane queues up to QK accepted pseudo-sources, each as (C, d_C, d*, source) and
-// (q, L), d* the depth of the common ancestor of S and C found when C was accepted.
-// The C side of a ray is generated by parent links (C, then the siblings of C and
-// of its ancestors, deep to shallow, the same cells and order as the walk path
-// gives), so a queued ray no longer depends on the walk path and can wait while the
-// walk moves on. The warp traces all queued rays of all lanes in one loop in which
-// a lane that finishes a ray starts its next queued one, so lanes idle only at the
-// end of the queue. Every lane must call it.
-template <bool MOM, bool STOP, int NB, bool SUB, bool CNT, bool TD>
-__device__ __forceinline__ void warp_rays_q(const TreeView& T, const WalkParams& P,
-                                            const float px, const float py, const float pz,
-                                            const int S, const int dS, const int* anc, int* rst,
-                                            const int4* qc, const float4* qq, const int qn,
-                                            const int box_limit, int* status, SinkCounters& cnt,
-                                            CSum* F, Moments* mom, const int si) {
-  const unsigned FULL = 0xffffffffu;
-  int qi = 0;             // next queued ray
-  bool active = false;    // a ray is being traced
-  float dx = 0.0f, dy = 0.0f, dz = 0.0f, s2 = 1.0f, len = 1.0f, ix = 0.0f, iy = 0.0f, iz = 0.0f;
-  float L = 0.0f;
-  bool nz = false;
-  int C = 0, src_j = -1, nCs = 0, nSs = 0, nb = 0, dstar = 0, base1 = S;
-  int b = 0, rsp = 0, slot = -1, boxes = 0;
-  int cur = 0, par = 0;   // the C-side cell whose sibling comes next, and its parent
-  KSum tau;
-  KSum taub[NB];
-  bool cut = false;
-  bool need_sub = false;  // (SUB) this step's leaf is traced through its particles
-  int sub_box = 0;
-  float sub_t0 = 0.0f, sub_t1 = 0.0f;
-  while (__any_sync(FULL, active || qi < qn)) {
-    if (!active && qi < qn) {
-      // the lane's next queued ray
-      const int4 e = qc[qi];
-      const float4 g = qq[qi];
-      ++qi;
-      C = e.x;
-      dstar = e.z;
-      src_j = e.w;
-      L = g.w;
-      dx = __fsub_rn(g.x, px);
-      dy = __fsub_rn(g.y, py);
-      dz = __fsub_rn(g.z, pz);
-      s2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-      if (!(s2 < P.smin2)) {  // a source on top of the sink adds nothing
-        active = true;
-        len = __fsqrt_rn(s2);
-        ix = dx != 0.0f ? __frcp_rn(dx) : 0.0f;
-        iy = dy != 0.0f ? __frcp_rn(dy) : 0.0f;
-        iz = dz != 0.0f ? __frcp_rn(dz) : 0.0f;
-        nz = dx != 0.0f && dy != 0.0f && dz != 0.0f;
-        nCs = 0;
-        nSs = 0;
-        if (C == S) {
-          nb = 1;
-          base1 = S;
-        } else if (TD) {
-          nb = 1;
-          base1 = anc[dstar];  // the common ancestor A
-        } else {
-          nCs = e.y - dstar - 1;
-          nSs = dS - dstar - 1;
-          nb = nCs + nSs + 2;
-        }
-        b = 0;
-        rsp = 0;
-        slot = -1;
-        boxes = 0;
-        cur = C;
-        par = nCs > 0 ? __ldg(&T.nT[C].y) : 0;
-        tau = KSum();
-        for (int k = 0; k < NB; ++k) taub[k] = KSum();
-        cut = false;
-      }
-    } else if (active) {
-      const bool from_stack = b >= nb && (rsp > 0 || slot >= 0);  // base segments first
-      if (!from_stack && b >= nb) {
-        // the ray is complete: its term of Eq. simpint
-        if (STOP && cut) {
-          if (CNT) ++cnt.cut;
-        } else if (NB > 1) {
-          const float4 Lb = src_j >= 0 ? __ldg(&T.bLs[src_j]) : __ldg(&T.bLc[C]);
-          F[0].add(Lb.x * expf(-taub[0].get()) / (kFourPi * s2));
-          F[1].add(Lb.y * expf(-taub[1].get()) / (kFourPi * s2));
-          if (NB > 2) {
-            F[NB > 2 ? 2 : 0].add(Lb.z * expf(-taub[NB > 2 ? 2 : 0].get()) / (kFourPi * s2));
-            F[NB > 2 ? 3 : 0].add(Lb.w * expf(-taub[NB > 2 ? 3 : 0].get()) / (kFourPi * s2));
-          }
-        } else {
-          const float f = L * expf(-tau.get()) / (kFourPi * s2);
-          F[0].add(f);
-          if (MOM) {
-            const float il = 1.0f / len;
-            const float n0 = -dx * il, n1 = -dy * il, n2 = -dz * il;
-            mom->v[0].add(f * n0);
-            mom->v[1].add(f * n1);
-            mom->v[2].add(f * n2);
-            mom->v[3].add(f * n0 * n0);
-            mom->v[4].add(f * n1 * n1);
-            mom->v[5].add(f * n2 * n2);
-            mom->v[6].add(f * n0 * n1);
-            mom->v[7].add(f * n0 * n2);
-            mom->v[8].add(f * n1 * n2);
-          }
-        }
-        if (CNT) ++cnt.rays;
-        active = false;
-      } else {
-        int box;
-        if (from_stack) {
-          if (slot >= 0) {
-            box = slot;
-            slot = -1;
-          } else {
-            // a refined cell's pair of children: clip the lower, keep the upper
-            box = ~rst[--rsp];
-            slot = box + 1;
-          }
-        } else {
-          if (nb == 1) {
-            box = base1;
-          } else if (b <= nCs) {  // C, then the siblings up C's path by parent links
-            if (b == 0) {
-              box = C;
-            } else {
-              box = cur ^ 1;
-              cur = par;
-              if (b < nCs) par = __ldg(&T.nT[cur].y);  // used by the next step
-            }
-          } else {  // the siblings down S's path, then S = anc[dS]
-            const int j = b - nCs;
-            box = anc[dstar + 1 + min(j, nSs)] ^ (j <= nSs ? 1 : 0);
-          }
-          ++b;
-        }
-        // Each iteration clips one base segment or one child of a pushed pair, and the
-        // pushes are capped by box_limit below, so a ray ends after at most
-        // nb + 2 box_limit iterations (the walk's hang guard).
-        const float4 a = __ldg(&T.nA[box]);
-        const float4 bb = __ldg(&T.nB[box]);
-        float t0 = 0.0f, t1 = 1.0f;
-        bool miss = false;
-        if (nz) {  // no axis along which the ray stays still: no face tests
-          slab_nz(a.x, bb.x, px, ix, t0, t1);
-          slab_nz(a.y, bb.y, py, iy, t0, t1);
-          slab_nz(a.z, bb.z, pz, iz, t0, t1);
-        } else {
-          slab(a.x, bb.x, px, dx, ix, t0, t1, miss);
-          slab(a.y, bb.y, py, dy, iy, t0, t1, miss);
-          slab(a.z, bb.z, pz, dz, iz, t0, t1, miss);
-        }
-        const float l = (!miss && t1 > t0) ? __fmul_rn(__fsub_rn(t1, t0), len) : 0.0f;
-        if (CNT) ++cnt.clip;
-        if (l > 0.0f) {
-          bool pushed = false;
-          if (P.tau_ref <= 0.0f || __fmul_rn(bb.w, l) > P.tau_ref) {
-            const int child = __ldg(&T.nT[box].x);
-            if (child >= 0) {
-              if (rsp + 1 > kRayStack) {
-                atomicOr(status, kStatusStackOverflow);
-                active = false;
-              } else if (++boxes > box_limit) {
-                atomicOr(status, kStatusIterationLimit);
-                active = false;
-              } else {
-                if (CNT) ++cnt.ref;
-                rst[rsp++] = ~child;  // both children, clipped after the base segments
-              }
-              pushed = true;
-            }
-          }
-          if (!pushed) {
-            if (NB > 1) {
-              const float4 ab = __ldg(&T.bA[box]);
-              taub[0].add(__fmul_rn(ab.x, l));
-              taub[1].add(__fmul_rn(ab.y, l));
-              if (NB > 2) {
-                taub[NB > 2 ? 2 : 0].add(__fmul_rn(ab.z, l));
-                taub[NB > 2 ? 3 : 0].add(__fmul_rn(ab.w, l));
-              }
-            } else if (SUB && (P.tau_ref <= 0.0f ||
-                               __fmul_rn(__ldg(&T.dbk[box]), l) > P.tau_ref)) {
-              // a bucket that still asks for refinement: its particles are traced by
-              // the whole warp at the end of this step
-              need_sub = true;
-              sub_box = box;
-              sub_t0 = t0;
-              sub_t1 = t1;
-              if (CNT) ++cnt.sub;
-            } else {
-              tau.add(__fmul_rn(a.w, l));
-            }
-            if (STOP && tau.get() > P.tau_stop) {
-              cut = true;  // the rest of the ray is not traced
-              b = nb;
-              rsp = 0;
-              slot = -1;
-            }
-            if (CNT) ++cnt.segs;
-          }
-        }
-      }
-    }
-    if (SUB) {
-      // the leaves of this step that need the particle trace, one after another
-      unsigned m = __ballot_sync(FULL, need_sub);
-      while (m) {
-        const int src = __ffs(m) - 1;
-        m &= m - 1u;
-        const float t = sub_bucket_tau_warp(T, src, sub_box, si, px, py, pz, dx, dy, dz, s2, len,
-                                            sub_t0, sub_t1);
-        if ((int)(threadIdx.x & 31u) == src) tau.add(t);
-      }
-      need_sub = false;
-    }
-  }
-}
-
 // Background sources (Sec. 2.2.4): the centre of luminosity c (s.xyz) of an accepted
 // cell moved radially onto the sphere of radius P.bg_radius around the domain centre
 // o (side / 2 in coordinates relative to the lower corner), in fp32 as d = c - o,
@@ -1284,14 +1065,6 @@ __device__ __forceinline__ void bg_move(const TreeView& T, const WalkParams& P, 
   }
 }
 
-// Depth of the common ancestor of S and a cell at depth dC from the common-prefix mask
-// (bit d: the cell's ancestor at depth d is S's ancestor at depth d).
-__device__ __forceinline__ int common_depth(unsigned long long onp, int dC, int dS) {
-  const int mn = dC < dS ? dC : dS;
-  const unsigned long long m = onp & ((2ull << mn) - 1ull);  // mn <= 62
-  return __ffsll((long long)~m) - 2;
-}
-
 // The hot path for the 32 sinks of one warp (lane holds sorted position i if
 // `has`); every lane of the warp must call it. Accumulates the lane's flux in F.
 // MERGE = true: a lane that accepts a cell (or reaches a single source) does not
@@ -1305,7 +1078,7 @@ __device__ __forceinline__ int common_depth(unsigned long long onp, int dC, int 
 // q = o + d * (R / s); the ray then ends in the leaf that holds q, whose ancestors the
 // lane finds by descending the cut planes from the root and keeps for that ray.
 template <bool ADJ, bool MERGE, bool MOM = false, bool BG = false, bool STOP = false, int NB = 1,
-          bool SUB = false, bool CNT = true, bool TD = false, int QK = 0>
+          bool SUB = false, bool CNT = true, bool TD = false>
 __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P, const bool has,
                                           const int i, const float gk, WarpStack& ws,
                                           int* status, const AdjointArgs& J,
@@ -1345,16 +1118,6 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
   int cpath[BG ? kDepth : 1] = {};  // (BG) ancestors of the leaf holding the moved source
   int pC = 0, pdC = 0, psrc = -1;
   float pqx = 0.0f, pqy = 0.0f, pqz = 0.0f, pL = 0.0f;
-  // (QK > 0) this lane's queue of accepted pseudo-sources, traced by warp_rays_q
-  static_assert(QK == 0 || (MERGE && !ADJ), "queued rays: the merged flux walk only");
-  int4 qc[QK > 0 ? QK : 1];
-  float4 qq[QK > 0 ? QK : 1];
-  int qn = 0;
-  auto flushq = [&]() {
-    warp_rays_q<MOM, STOP, NB, SUB, CNT, TD>(T, P, px, py, pz, S, dS, anc, rst, qc, qq, qn,
-                                            box_limit, status, cnt, F, mom, i);
-    qn = 0;
-  };
   auto flush = [&]() {
     if (BG) {
       // a ray to a moved source uses its own path: the common-prefix mask of that
@@ -1385,7 +1148,7 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
     const unsigned M = ws.mask[sp];
     __syncwarp();
     // a pending ray reads the path up to its cell's depth: trace it before that changes
-    if (MERGE && QK == 0 && __any_sync(FULL, pnd && !pbg && pdC >= dX)) flush();
+    if (MERGE && __any_sync(FULL, pnd && !pbg && pdC >= dX)) flush();
     if (lane == 0) ws.path[dX] = X;
     const unsigned long long bit = 1ull << dX;
     if (has) on_path = (dX <= dS && anc[dX] == X) ? (on_path | bit) : (on_path & ~bit);
@@ -1407,23 +1170,7 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
     }
     const unsigned accM = __ballot_sync(FULL, acc);
     const unsigned opnM = __ballot_sync(FULL, opn);
-    if (MERGE && QK > 0) {
-      if (__any_sync(FULL, acc && qn == QK)) flushq();
-      if (acc) {
-        float qx = s.x, qy = s.y, qz = s.z;
-        int Cq = X, dCq = dX;
-        unsigned long long onp = on_path;
-        if (BG) {
-          bg_move(T, P, s, qx, qy, qz, Cq, dCq, cpath);
-          onp = 0;
-          const int mn = dCq < dS ? dCq : dS;
-          for (int d = 0; d <= mn && cpath[d] == anc[d]; ++d) onp |= 1ull << d;
-        }
-        qc[qn] = make_int4(Cq, dCq, common_depth(onp, dCq, dS), -1);
-        qq[qn] = make_float4(qx, qy, qz, s.w);
-        ++qn;
-      }
-    } else if (MERGE) {
+    if (MERGE) {
       if (__any_sync(FULL, acc && pnd)) flush();
       if (acc) {
         pnd = true;
@@ -1450,14 +1197,7 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
         for (int jj = t.z; jj < t.z + t.w; ++jj) {
           const float4 y = __ldg(&T.src[jj]);
           if (!(y.w > 0.0f)) continue;
-          if (MERGE && QK > 0) {
-            if (__any_sync(FULL, opn && qn == QK)) flushq();
-            if (opn) {
-              qc[qn] = make_int4(X, dX, common_depth(on_path, dX, dS), jj);
-              qq[qn] = y;
-              ++qn;
-            }
-          } else if (MERGE) {
+          if (MERGE) {
             if (__any_sync(FULL, opn && pnd)) flush();
             if (opn) {
               pnd = true;
@@ -1494,7 +1234,6 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
     }
   }
   if (MERGE && __any_sync(FULL, pnd)) flush();
-  if (QK > 0 && __any_sync(FULL, qn > 0)) flushq();
 }
 
 // 8 blocks of 128 per SM (at most 64 registers): measured 4% faster forward and 8%
@@ -1509,7 +1248,7 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
 // walks without counters fit 6 blocks (74 registers, no spills) instead of 4:
 // 245 ms against 262 ms for four bands on the clumpy workload.
 template <bool ADJ, bool MERGE, bool MOM = false, bool BG = false, bool STOP = false, int NB = 1,
-          bool SUB = false, bool CNT = true, bool TD = false, int QK = 0>
+          bool SUB = false, bool CNT = true, bool TD = false>
 __global__ void __launch_bounds__(128, SUB ? 4 : ADJ ? 8 : (NB > 1 ? (CNT ? 4 : 6) : (CNT ? 8 : 12))) walk_warp_kernel(TreeView T, const long long* sink_idx,
                                                         int n_sink, WalkParams P, SinkOut out,
                                                         unsigned long long* stats, int* status,
@@ -1533,7 +1272,7 @@ __global__ void __launch_bounds__(128, SUB ? 4 : ADJ ? 8 : (NB > 1 ? (CNT ? 4 : 
   CSum F[NB];
   Moments mom;
   if (__any_sync(0xffffffffu, has))
-    warp_walk<ADJ, MERGE, MOM, BG, STOP, NB, SUB, CNT, TD, QK>(T, P, has, i, g, ws, status, J, cnt, F,
+    warp_walk<ADJ, MERGE, MOM, BG, STOP, NB, SUB, CNT, TD>(T, P, has, i, g, ws, status, J, cnt, F,
                                                   MOM ? &mom : nullptr);
   if (MOM && has) {
 #pragma unroll
