@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -23,6 +24,41 @@ int status_to_error(int bits) {
 
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+constexpr int kMaxPoolDevices = 64;
+static std::mutex g_pool_mutex;
+static cudaMemPool_t g_pools[kMaxPoolDevices] = {};
+
+cudaError_t pool_malloc_async(void** p, size_t bytes, cudaStream_t s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxPoolDevices) return cudaMallocAsync(p, bytes, s);
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    if (!g_pools[dev]) {
+      cudaMemPoolProps props;
+      std::memset(&props, 0, sizeof(props));
+      props.allocType = cudaMemAllocationTypePinned;
+      props.handleTypes = cudaMemHandleTypeNone;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      cudaMemPool_t np = nullptr;
+      e = cudaMemPoolCreate(&np, &props);
+      if (e != cudaSuccess) return e;
+      unsigned long long keep = ~0ull;  // never trim: freed memory stays for reuse
+      e = cudaMemPoolSetAttribute(np, cudaMemPoolAttrReleaseThreshold, &keep);
+      if (e != cudaSuccess) {
+        cudaMemPoolDestroy(np);
+        return e;
+      }
+      g_pools[dev] = np;
+    }
+    pool = g_pools[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
 
 int cuda_to_error(cudaError_t e) {
   if (e == cudaSuccess) return TREVR_OK;
@@ -320,7 +356,7 @@ int trevr_compute_flux_backward(const trevr_tree* t, const long long* sink_idx, 
   // accumulators: G, a, b (3 per cell), e (per source), H (per cell prefix)
   const size_t words = 5 * nc + ns + nc;
   double* buf = nullptr;
-  cudaError_t err = cudaMallocAsync((void**)&buf, words * sizeof(double), s);
+  cudaError_t err = pool_malloc_async((void**)&buf, words * sizeof(double), s);
   if (err != cudaSuccess) {
     cudaGetLastError();
     return TREVR_ERR_OUT_OF_MEMORY;

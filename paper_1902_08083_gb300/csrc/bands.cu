@@ -140,8 +140,8 @@ int build_tree_bands_impl(const float* gas_xyz, const float* alpha_bands, const 
   const int n = (int)n_gas, ns = (int)n_src, nb = n_bands;
   float* lsum = nullptr;
   int* st = nullptr;
-  cudaError_t e = cudaMallocAsync(&lsum, sizeof(float) * (ns > 0 ? ns : 1), s);
-  if (e == cudaSuccess) e = cudaMallocAsync(&st, sizeof(int), s);
+  cudaError_t e = pool_malloc_async((void**)&lsum, sizeof(float) * (ns > 0 ? ns : 1), s);
+  if (e == cudaSuccess) e = pool_malloc_async((void**)&st, sizeof(int), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(int), s);
   if (e != cudaSuccess) {
     if (lsum) cudaFreeAsync(lsum, s);
@@ -179,8 +179,8 @@ int build_tree_bands_impl(const float* gas_xyz, const float* alpha_bands, const 
   e = cudaMalloc(&t->bA, sizeof(float4) * ncell);
   if (e == cudaSuccess) e = cudaMalloc(&t->bLc, sizeof(float4) * ncell);
   if (e == cudaSuccess) e = cudaMalloc(&t->bLs, sizeof(float4) * (ns > 0 ? ns : 1));
-  if (e == cudaSuccess) e = cudaMallocAsync(&as, sizeof(float) * n, s);
-  if (e == cudaSuccess) e = cudaMallocAsync(&mom, sizeof(BandMom) * ncell, s);
+  if (e == cudaSuccess) e = pool_malloc_async((void**)&as, sizeof(float) * n, s);
+  if (e == cudaSuccess) e = pool_malloc_async((void**)&mom, sizeof(BandMom) * ncell, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(t->bA, 0, sizeof(float4) * ncell, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(t->bLc, 0, sizeof(float4) * ncell, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(t->bLs, 0, sizeof(float4) * (ns > 0 ? ns : 1), s);

@@ -218,6 +218,11 @@ cudaError_t adjoint_finalize(const trevr_tree* t, const AdjointArgs& J, float* g
                              float* grad_alpha, double* H, cudaStream_t s);
 
 // ---- api.cu helpers
+// Stream-ordered allocation from the library's own memory pool on the current device.
+// The pool keeps freed memory for reuse (the process's default pool would return it to
+// the driver at every synchronisation, and every tree build would map its buffers
+// again). Free with cudaFreeAsync, or cudaFree.
+cudaError_t pool_malloc_async(void** p, size_t bytes, cudaStream_t s);
 int status_to_error(int status_bits);
 void note_launch(int n = 1);  // count kernels launched by the library
 int cuda_to_error(cudaError_t e);
