@@ -27,6 +27,14 @@
  *     word read back at the function's sync point; the kernels never trap.
  *     Outputs are undefined when the return value is not TREVR_OK.
  *   - Particle and source counts are limited to 2^30 (indices are 32-bit).
+ *   - Device memory: a tree's buffers, and the scratch of the tree build and of
+ *     the adjoint, come from a stream-ordered memory pool the library creates on
+ *     each device it is used on. The pool keeps memory that is freed (so that
+ *     the next build or backward call reuses it without mapping it again) until
+ *     the process exits.
+ *   - Positions inside the library are relative to the domain's lower corner
+ *     (x - lo), so fp32 rounding depends on the size of the domain, not on its
+ *     distance from the origin; outputs that are positions say so.
  */
 #ifndef TREVR_H
 #define TREVR_H
