@@ -144,8 +144,6 @@ TreeView trevr_tree::view() const {
   v.nbr = nbr;
   v.nbr_sp = nbr_sp;
   v.nbr_aw = nbr_aw;
-  v.nbr_chunk_first = nbr_chunk_first;
-  v.nbr_chunk = nbr_chunk;
   v.kint = kint;
   return v;
 }
@@ -637,7 +635,7 @@ void trevr_tree_free(trevr_tree* t) {
                   t->nglo, t->nghi,  t->src,    t->src_order, t->levels, t->d_n_nodes,
                   t->status, t->d_stats, t->src_leaf, t->nW, t->bA, t->bLc, t->bLs, t->sp, t->aw,
                   t->dbk, t->nbr_first, t->nbr, t->nbr_sp, t->nbr_aw,
-                  t->nbr_chunk_first, t->nbr_chunk, t->kint};
+                  t->kint};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   cudaSetDevice(cur);

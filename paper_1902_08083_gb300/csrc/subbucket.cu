@@ -181,45 +181,6 @@ __global__ void kint_table_kernel(float* __restrict__ tab) {
   }
 }
 
-// chunks of 32 entries per leaf list (counted from the list's start)
-__global__ void chunk_count_kernel(const unsigned* __restrict__ first, int n_cells,
-                                   unsigned* __restrict__ chunk_count) {
-  for (int X = blockIdx.x * blockDim.x + threadIdx.x; X < n_cells; X += gridDim.x * blockDim.x)
-    chunk_count[X] = (first[X + 1] - first[X] + 31u) / 32u;
-}
-
-// The sphere of each chunk: centre at the middle of its entries' bounding box, radius
-// the largest |x_j - c| + 2 h_j over its entries, widened by 1e-5 relative and the
-// pad: a chord at least that far from the centre meets no entry's support.
-__global__ void chunk_sphere_kernel(const unsigned* __restrict__ first,
-                                    const unsigned* __restrict__ chunk_first,
-                                    const float4* __restrict__ nsp, int n_cells, float pad,
-                                    float4* __restrict__ chunk) {
-  for (int X = blockIdx.x * blockDim.x + threadIdx.x; X < n_cells; X += gridDim.x * blockDim.x) {
-    const unsigned k0 = first[X], k1 = first[X + 1];
-    unsigned c = chunk_first[X];
-    for (unsigned b = k0; b < k1; b += 32u, ++c) {
-      const unsigned e = b + 32u < k1 ? b + 32u : k1;
-      float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-      for (unsigned k = b; k < e; ++k) {
-        const float4 q = nsp[k];
-        lo[0] = fminf(lo[0], q.x); hi[0] = fmaxf(hi[0], q.x);
-        lo[1] = fminf(lo[1], q.y); hi[1] = fmaxf(hi[1], q.y);
-        lo[2] = fminf(lo[2], q.z); hi[2] = fmaxf(hi[2], q.z);
-      }
-      const float cx = 0.5f * (lo[0] + hi[0]), cy = 0.5f * (lo[1] + hi[1]),
-                  cz = 0.5f * (lo[2] + hi[2]);
-      float r = 0.0f;
-      for (unsigned k = b; k < e; ++k) {
-        const float4 q = nsp[k];
-        const float dx = q.x - cx, dy = q.y - cy, dz = q.z - cz;
-        r = fmaxf(r, sqrtf(dx * dx + dy * dy + dz * dz) + 2.0f * q.w);
-      }
-      chunk[c] = make_float4(cx, cy, cz, fmaf(r, 1.00001f, pad));
-    }
-  }
-}
-
 inline int grid_of(long long n, int threads) {
   long long g = (n + threads - 1) / threads;
   return (int)(g < 1 ? 1 : (g > 8192 ? 8192 : g));
@@ -244,8 +205,6 @@ int set_smoothing_impl(trevr_tree* t, const float* h, cudaStream_t s) {
   free_dev(t->nbr);
   free_dev(t->nbr_sp);
   free_dev(t->nbr_aw);
-  free_dev(t->nbr_chunk_first);
-  free_dev(t->nbr_chunk);
   free_dev(t->kint);
   t->n_nbr = 0;
   float* hmax = nullptr;
@@ -318,30 +277,6 @@ int set_smoothing_impl(trevr_tree* t, const float* h, cudaStream_t s) {
         e = cudaStreamSynchronize(s);
         t->n_nbr = total;
       }
-      // the chunk spheres: a chunk count per cell, their prefix sum, the spheres
-      unsigned n_chunks = 0;
-      if (e == cudaSuccess && !bad)
-        e = cudaMalloc(&t->nbr_chunk_first, sizeof(unsigned) * (ncell + 1));
-      if (e == cudaSuccess && !bad) {
-        chunk_count_kernel<<<grid_of((long long)ncell, 256), 256, 0, s>>>(
-            t->nbr_first, (int)ncell, t->nbr_chunk_first);
-        note_launch();
-        e = cudaMemsetAsync(t->nbr_chunk_first + ncell, 0, sizeof(unsigned), s);
-        if (e == cudaSuccess) {
-          exclusive_scan_u32(t->nbr_chunk_first, (int)ncell + 1, scratch, s);
-          e = cudaMemcpyAsync(&n_chunks, t->nbr_chunk_first + ncell, sizeof(unsigned),
-                              cudaMemcpyDeviceToHost, s);
-        }
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e == cudaSuccess)
-          e = cudaMalloc(&t->nbr_chunk, sizeof(float4) * (n_chunks > 0 ? n_chunks : 1));
-        if (e == cudaSuccess) {
-          chunk_sphere_kernel<<<grid_of((long long)ncell, 128), 128, 0, s>>>(
-              t->nbr_first, t->nbr_chunk_first, t->nbr_sp, (int)ncell, A.pad, t->nbr_chunk);
-          note_launch();
-          e = cudaStreamSynchronize(s);
-        }
-      }
     }
   }
   if (hmax) cudaFree(hmax);
@@ -355,8 +290,6 @@ int set_smoothing_impl(trevr_tree* t, const float* h, cudaStream_t s) {
     free_dev(t->nbr);
     free_dev(t->nbr_sp);
     free_dev(t->nbr_aw);
-    free_dev(t->nbr_chunk_first);
-    free_dev(t->nbr_chunk);
     free_dev(t->kint);
     t->n_nbr = 0;
     if (e == cudaErrorMemoryAllocation) return TREVR_ERR_OUT_OF_MEMORY;

@@ -70,10 +70,6 @@ struct TreeView {
   const int* nbr;
   const float4* nbr_sp;  // per list entry: the neighbour's (x, y, z, h), contiguous per leaf
   const float* nbr_aw;   // per list entry: the neighbour's alpha * w
-  // per leaf, its list cut into chunks of 32 entries from the list's start: the
-  // sphere (centre, radius) holding every chunk entry's support
-  const unsigned* nbr_chunk_first;
-  const float4* nbr_chunk;
   const float* kint;   // kernel-integral table, (kKintNX + 1) x (kKintNS + 1), sigma fastest
 };
 
@@ -136,8 +132,6 @@ struct trevr_tree {
   int* nbr;          // sorted particle indices whose kernel support meets the leaf
   float4* nbr_sp;    // the same entries' (x, y, z, h), so a leaf's list is read coalesced
   float* nbr_aw;     // the same entries' alpha * w
-  unsigned* nbr_chunk_first;  // per cell + 1: start of the leaf's chunk spheres
-  float4* nbr_chunk;          // per chunk of 32 list entries: (centre, radius) of their supports
   long long n_nbr;
   float* kint;       // kernel-integral table of the sub-bucket trace (see TreeView)
   int h_levels[2 * trevr::kMaxLevels];  // host copy of the level ranges

@@ -678,18 +678,7 @@ __device__ __forceinline__ float sub_bucket_tau_warp(const TreeView& T, int src,
   float part = 0.0f;
   int qn = 0;  // queued entries (warp-uniform)
   const unsigned k0 = __ldg(&T.nbr_first[box]), k1 = __ldg(&T.nbr_first[box + 1]);
-  unsigned chunk = __ldg(&T.nbr_chunk_first[box]);
-  for (unsigned base = k0; base < k1; base += 32u, ++chunk) {
-    // the round's 32 entries lie in one chunk sphere: when the chord keeps out of it,
-    // no entry's support reaches the chord (the same for every lane: the round is
-    // skipped by the whole warp)
-    {
-      const float4 c = __ldg(&T.nbr_chunk[chunk]);
-      const float ux = c.x - px, uy = c.y - py, uz = c.z - pz;
-      const float tcl = fminf(fmaxf((ux * dx + uy * dy + uz * dz) * inv_s2, t0), t1);
-      const float ex = ux - tcl * dx, ey = uy - tcl * dy, ez = uz - tcl * dz;
-      if (ex * ex + ey * ey + ez * ez >= c.w * c.w) continue;
-    }
+  for (unsigned base = k0; base < k1; base += 32u) {
     const unsigned k = base + lane;
     bool pass = false;
     float a = 0.0f, b2 = 0.0f, sa = 0.0f, sb = 0.0f, H = 1.0f;
