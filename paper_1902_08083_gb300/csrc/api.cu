@@ -126,6 +126,7 @@ TreeView trevr_tree::view() const {
   v.nS = nS;
   v.nT = nT;
   v.nl2 = nl2;
+  v.nSP = nSP;
   v.ndepth = ndepth;
   v.nglo = nglo;
   v.nfirst = nfirst;
@@ -630,7 +631,7 @@ void trevr_tree_free(trevr_tree* t) {
   cudaGetDevice(&cur);
   cudaSetDevice(t->device);
   cudaDeviceSynchronize();
-  void* ptrs[] = {t->key, t->perm,   t->rank,   t->leaf_of, t->pos,    t->w,      t->nA,
+  void* ptrs[] = {t->nSP, t->key, t->perm,   t->rank,   t->leaf_of, t->pos,    t->w,      t->nA,
                   t->nB,  t->nS,     t->nT,     t->nl2,     t->ndepth, t->nfirst, t->ncount,
                   t->nglo, t->nghi,  t->src,    t->src_order, t->levels, t->d_n_nodes,
                   t->status, t->d_stats, t->src_leaf, t->nW, t->bA, t->bLc, t->bLs, t->sp, t->aw,

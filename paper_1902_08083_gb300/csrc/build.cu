@@ -489,6 +489,7 @@ struct MomentArrays {
   float4* nB;
   float4* nS;
   float* nl2;
+  float2* nSP;
   float h;
 };
 
@@ -589,6 +590,14 @@ __device__ __forceinline__ void moments_cell(const MomentArrays& A, int X) {
     A.nB[X] = make_float4(bhi[0], bhi[1], bhi[2], dal);
     A.nS[X] = make_float4(c[0], c[1], c[2], Lf);
     A.nl2[X] = l2;
+    if (t.x >= 0) {
+      const int ax = A.nglo[X].w;
+      const int4 u = A.nglo[t.x + 1];
+      A.nSP[X] = make_float2(rel_plane(A.h, ax == 0 ? u.x : (ax == 1 ? u.y : u.z)),
+                             __int_as_float(ax));
+    } else {
+      A.nSP[X] = make_float2(0.0f, __int_as_float(-1));
+    }
   }
 }
 
@@ -811,6 +820,7 @@ int build_tree_impl(const float* gas_xyz, const float* alpha, const float* weigh
   t->nB = keep.get<float4>(ncell);
   t->nS = keep.get<float4>(ncell);
   t->nl2 = keep.get<float>(ncell);
+  t->nSP = keep.get<float2>(ncell);
   t->nW = keep.get<double>(ncell);
   Moments* mom = tmp.get<Moments>(ncell);
   if (!keep.ok || !tmp.ok) {
@@ -822,6 +832,7 @@ int build_tree_impl(const float* gas_xyz, const float* alpha, const float* weigh
   cudaMemsetAsync(t->nB, 0, sizeof(float4), s);
   cudaMemsetAsync(t->nS, 0, sizeof(float4), s);
   cudaMemsetAsync(t->nl2, 0, sizeof(float), s);
+  cudaMemsetAsync(t->nSP, 0, sizeof(float2), s);
   cudaMemsetAsync(t->nW, 0, sizeof(double), s);
   MomentArrays MA;
   MA.nT = t->nT;
@@ -839,6 +850,7 @@ int build_tree_impl(const float* gas_xyz, const float* alpha, const float* weigh
   MA.nB = t->nB;
   MA.nS = t->nS;
   MA.nl2 = t->nl2;
+  MA.nSP = t->nSP;
   MA.h = t->h;
   // one launch per level, sized to the level (measured faster than one cooperative
   // launch over all levels: 0.26 against 0.66 ms per build at 2^22)

@@ -49,6 +49,7 @@ struct TreeView {
   const float4* nS;  // (cen.x, cen.y, cen.z, L)
   const int4* nT;    // (child or -1, parent, src_first, src_count)
   const float* nl2;  // l^2 (furthest vertex from the centre of luminosity)
+  const float2* nSP; // (split plane relative to lo, split axis as int bits), internal cells
   const int* ndepth;
   const int4* nglo;  // integer box lower corner, w = split axis (-1 for a leaf)
   const int* nfirst;
@@ -110,6 +111,7 @@ struct trevr_tree {
   float4* nS;
   int4* nT;
   float* nl2;
+  float2* nSP;
   int* ndepth;
   int* nfirst;
   int* ncount;

