@@ -577,7 +577,7 @@ def _bench_glass(args):
 
 def run_ours(args):
     import torch
-    from paper_1902_08083_gb300 import trevr
+    from paper_1902_08083_gb300 import autotune, trevr
 
     rank, world, local = _dist()
     if world > 1:
@@ -596,20 +596,25 @@ def run_ours(args):
     flux = torch.empty(n, dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
+    shape = {}  # the walk's launch shape, picked by the autotuner below
+
     def step(timed_events=None):
         tree = trevr.build_tree(g["gas_xyz"], g["alpha"], g["src_xyz"], g["src_lum"],
                                 lo=P["lo"], side=P["side"], bucket=P["bucket"], stream=stream)
         if timed_events is not None:
             timed_events[1].record(stream)
-        trevr.compute_flux(tree, P["theta"], P["tau_ref"], out=flux, stream=stream)
+        trevr.compute_flux(tree, P["theta"], P["tau_ref"], out=flux, stream=stream, **shape)
         if timed_events is not None:
             timed_events[2].record(stream)
         return tree
 
+    # the walk's shape from the autotuner, timed on this tree (untimed here); then
     # counters (untimed) for the algorithmic-bytes figure
     tree = step()
+    tuned = autotune.tune_walk(tree, P["theta"], P["tau_ref"], use_cache=False)
+    shape.update(walk_variant=tuned["walk_variant"], sinks_per_warp=tuned["sinks_per_warp"])
     _, st = trevr.compute_flux(tree, P["theta"], P["tau_ref"], out=flux, stats=True,
-                               stream=stream)
+                               stream=stream, **shape)
     tree.free()
     for _ in range(args.warmup):
         step().free()
@@ -654,7 +659,7 @@ def run_ours(args):
             dbuf[k].copy_(host[k], non_blocking=True)
         tr = trevr.build_tree(dbuf["gas_xyz"], dbuf["alpha"], dbuf["src_xyz"], dbuf["src_lum"],
                               lo=P["lo"], side=P["side"], bucket=P["bucket"], stream=stream)
-        trevr.compute_flux(tr, P["theta"], P["tau_ref"], out=flux, stream=stream)
+        trevr.compute_flux(tr, P["theta"], P["tau_ref"], out=flux, stream=stream, **shape)
         hflux.copy_(flux, non_blocking=True)
         stream.synchronize()
         tr.free()
@@ -689,8 +694,10 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     sm_mhz = clk.get("sm_mhz") or _peaks_clock()
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    roofline = _issue_roofline(_kernel_profile("walk_warp_kernel_issue.json"), n, t_walk,
-                               sm_mhz, n_sm, alg_bytes, peak, peak_kind,
+    # the committed counters are those of the merged-ray walk (variant 3)
+    prof = (_kernel_profile("walk_warp_kernel_issue.json")
+            if shape["walk_variant"] in (0, 3) else None)
+    roofline = _issue_roofline(prof, n, t_walk, sm_mhz, n_sm, alg_bytes, peak, peak_kind,
                                "walk_warp_kernel, variant 3 (warp-shared walk, merged rays, "
                                "flux, no counters)")
 
@@ -706,6 +713,9 @@ def run_ours(args):
                          "refinements": st["refine_expansions"] / n,
                          "cells_clipped": st["cells_clipped"] / n},
             "roofline": roofline,
+            "walk_autotune": {"walk_variant": tuned["walk_variant"],
+                              "sinks_per_warp": tuned["sinks_per_warp"],
+                              "ms_per_shape": tuned["table"]},
             "e2e": {"value": job_value(n, world, t_e2e), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "clocks": clk}
