@@ -1277,10 +1277,12 @@ __device__ __forceinline__ void warp_walk(const TreeView& T, const WalkParams& P
 // blocks were slower (141 ms).
 // CNT = false keeps no per-sink counters; the fluxes are bit-identical. The band
 // walks without counters fit 6 blocks (74 registers, no spills) instead of 4:
-// 245 ms against 262 ms for four bands on the clumpy workload.
+// 245 ms against 262 ms for four bands on the clumpy workload. The sub-bucket walk
+// runs 8 blocks (64 registers, spilling): 325.6 ms against 343.0 ms at 4 blocks
+// (114 registers) on 2^18 particles, without counters.
 template <bool ADJ, bool MERGE, bool MOM = false, bool BG = false, bool STOP = false, int NB = 1,
           bool SUB = false, bool CNT = true, bool TD = false>
-__global__ void __launch_bounds__(128, SUB ? 4 : ADJ ? 8 : (NB > 1 ? (CNT ? 4 : 6) : (CNT ? 8 : 12))) walk_warp_kernel(TreeView T, const long long* sink_idx,
+__global__ void __launch_bounds__(128, SUB ? 8 : ADJ ? 8 : (NB > 1 ? (CNT ? 4 : 6) : (CNT ? 8 : 12))) walk_warp_kernel(TreeView T, const long long* sink_idx,
                                                         int n_sink, WalkParams P, SinkOut out,
                                                         unsigned long long* stats, int* status,
                                                         AdjointArgs J) {
@@ -1473,9 +1475,14 @@ cudaError_t launch_walk(const TreeView& T, const long long* sink_idx, int n_sink
   if (n_sink <= 0) return cudaSuccess;
   (void)block_size;
   if (wp.sub_bucket) {
-    walk_warp_kernel<false, true, false, false, false, 1, true><<<(n_sink + 127) / 128, 128, 0, s>>>(
-        T, sink_idx, n_sink, wp, SinkOut{flux_out, counters, nullptr, nullptr, n_sink}, stats,
-        status, AdjointArgs{});
+    if (counters || stats)
+      walk_warp_kernel<false, true, false, false, false, 1, true><<<(n_sink + 127) / 128, 128, 0, s>>>(
+          T, sink_idx, n_sink, wp, SinkOut{flux_out, counters, nullptr, nullptr, n_sink}, stats,
+          status, AdjointArgs{});
+    else
+      walk_warp_kernel<false, true, false, false, false, 1, true, false><<<(n_sink + 127) / 128, 128, 0, s>>>(
+          T, sink_idx, n_sink, wp, SinkOut{flux_out, nullptr, nullptr, nullptr, n_sink}, nullptr,
+          status, AdjointArgs{});
     note_launch();
     return cudaGetLastError();
   }
