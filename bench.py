@@ -775,6 +775,33 @@ def run_profile(args):
     tree.free()
 
 
+def run_profile_sub(args):
+    """A short program for ncu on the sub-bucket walk: the 2^18-particle sub-bucket
+    workload, its neighbour lists, one walk with counters (launch 0, counters
+    printed) and one without (launch 1, the one to capture:
+    -k regex:walk_warp_kernel -s 1 -c 1)."""
+    import torch
+    from paper_1902_08083_gb300 import trevr
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    P = workloads.sub_bucket_problem(n_gas=1 << 18, n_src=1024, seed=12)
+    t = {k: torch.from_numpy(np.ascontiguousarray(P[k])).to(dev)
+         for k in ("gas_xyz", "alpha", "src_xyz", "src_lum", "weight", "hsml")}
+    tree = trevr.build_tree(t["gas_xyz"], t["alpha"], t["src_xyz"], t["src_lum"],
+                            weight=t["weight"], lo=P["lo"], side=P["side"], bucket=P["bucket"])
+    tree.set_smoothing(t["hsml"])
+    _, st = trevr.compute_flux(tree, P["theta"], P["tau_ref"], sub_bucket=1, stats=True)
+    f = trevr.compute_flux(tree, P["theta"], P["tau_ref"], sub_bucket=1)
+    torch.cuda.synchronize()
+    n = int(P["gas_xyz"].shape[1])
+    print(json.dumps({"profile": "sub_bucket", "sinks": n,
+                      "cells_tested": st["src_nodes_visited"],
+                      "cells_clipped": st["cells_clipped"], "segments": st["segments"],
+                      "sub_bucket_segments": st["sub_bucket_segments"],
+                      "flux_sum": float(f.double().sum())}), flush=True)
+    tree.free()
+
+
 def run_profile_batched(args):
     """A short program for ncu on the batched walk: the 64 boxes, the autotuned launch
     shape, one batched call with counters (launch 0, counters printed) and one without
@@ -829,6 +856,8 @@ def main():
                     help="build once and run the walk twice on --sink-sample sinks (for ncu)")
     ap.add_argument("--profile-batched", action="store_true",
                     help="the 64 boxes: one batched walk with counters, one without (for ncu)")
+    ap.add_argument("--profile-sub", action="store_true",
+                    help="the sub-bucket workload: one walk with counters, one without (for ncu)")
     ap.add_argument("--sink-sample", type=int, default=1 << 20)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -837,6 +866,8 @@ def main():
         run_profile(args)
     elif args.profile_batched:
         run_profile_batched(args)
+    elif args.profile_sub:
+        run_profile_sub(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -142,10 +142,9 @@ TreeView trevr_tree::view() const {
   v.aw = aw;
   v.dbk = dbk;
   v.nbr_first = nbr_first;
-  v.nbr = nbr;
+  v.nbr_ja = nbr_ja;
   v.nbr_sp = nbr_sp;
-  v.nbr_aw = nbr_aw;
-  v.kint = kint;
+  v.kint4 = kint4;
   return v;
 }
 
@@ -635,8 +634,7 @@ void trevr_tree_free(trevr_tree* t) {
                   t->nB,  t->nS,     t->nT,     t->nl2,     t->ndepth, t->nfirst, t->ncount,
                   t->nglo, t->nghi,  t->src,    t->src_order, t->levels, t->d_n_nodes,
                   t->status, t->d_stats, t->src_leaf, t->nW, t->bA, t->bLc, t->bLs, t->sp, t->aw,
-                  t->dbk, t->nbr_first, t->nbr, t->nbr_sp, t->nbr_aw,
-                  t->kint};
+                  t->dbk, t->nbr_first, t->nbr_ja, t->nbr_sp, t->kint4};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   cudaSetDevice(cur);

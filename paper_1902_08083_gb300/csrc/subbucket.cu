@@ -70,10 +70,9 @@ struct NbrArgs {
   float pad;         // absolute slack added to every support radius
   unsigned* count;   // count pass: per cell
   const unsigned* first;  // fill pass: per cell start
-  int* nbr;               // fill pass: output (sorted particle index)
   const float* aw;        // per sorted particle alpha * w
-  float4* nbr_sp;         // fill pass: output, the entry's (x, y, z, h)
-  float* nbr_aw;          // fill pass: output, the entry's alpha * w
+  int2* nbr_ja;           // fill pass: output, the entry's sorted index and alpha * w (bits)
+  float4* nbr_sp;         // fill pass: output, the entry's (x, y, z, 1/h)
   int* status;
 };
 
@@ -120,9 +119,8 @@ __global__ void nbr_kernel(NbrArgs A) {
         const float r = fmaf(2.0f * q.w, 1.00001f, A.pad);
         if (ex * ex + ey * ey + ez * ez < r * r) {
           if (FILL && out < out_end) {
-            A.nbr[out] = i;
-            A.nbr_sp[out] = q;
-            A.nbr_aw[out] = A.aw[i];
+            A.nbr_ja[out] = make_int2(i, __float_as_int(A.aw[i]));
+            A.nbr_sp[out] = make_float4(q.x, q.y, q.z, __frcp_rn(q.w));
             ++out;
           }
           ++c;
@@ -181,6 +179,18 @@ __global__ void kint_table_kernel(float* __restrict__ tab) {
   }
 }
 
+// the table by cells: the four corner values of each cell of the grid in one record,
+// so that a bilinear lookup reads 16 bytes once
+__global__ void kint_cells_kernel(const float* __restrict__ tab, float4* __restrict__ cells) {
+  const int n = kKintNX * kKintNS;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int i = e / kKintNS, j = e - i * kKintNS;
+    const float* r0 = tab + (size_t)i * (kKintNS + 1) + j;
+    const float* r1 = r0 + (kKintNS + 1);
+    cells[e] = make_float4(r0[0], r0[1], r1[0], r1[1]);
+  }
+}
+
 inline int grid_of(long long n, int threads) {
   long long g = (n + threads - 1) / threads;
   return (int)(g < 1 ? 1 : (g > 8192 ? 8192 : g));
@@ -202,12 +212,12 @@ int set_smoothing_impl(trevr_tree* t, const float* h, cudaStream_t s) {
   free_dev(t->aw);
   free_dev(t->dbk);
   free_dev(t->nbr_first);
-  free_dev(t->nbr);
+  free_dev(t->nbr_ja);
   free_dev(t->nbr_sp);
-  free_dev(t->nbr_aw);
-  free_dev(t->kint);
+  free_dev(t->kint4);
   t->n_nbr = 0;
   float* hmax = nullptr;
+  float* tab = nullptr;  // the kernel-integral table on the grid's nodes, before packing
   unsigned* scratch = nullptr;
   int* st = nullptr;
   cudaError_t e = cudaMalloc(&t->sp, sizeof(float4) * n);
@@ -217,8 +227,8 @@ int set_smoothing_impl(trevr_tree* t, const float* h, cudaStream_t s) {
   if (e == cudaSuccess) e = cudaMalloc(&hmax, sizeof(float) * ncell);
   if (e == cudaSuccess) e = cudaMalloc(&scratch, sizeof(unsigned) * scan_scratch_words((int)ncell + 1));
   if (e == cudaSuccess) e = cudaMalloc(&st, sizeof(int));
-  if (e == cudaSuccess)
-    e = cudaMalloc(&t->kint, sizeof(float) * (size_t)(kKintNX + 1) * (kKintNS + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&tab, sizeof(float) * (size_t)(kKintNX + 1) * (kKintNS + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&t->kint4, sizeof(float4) * (size_t)kKintNX * kKintNS);
   if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(int), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(t->nbr_first, 0, sizeof(unsigned) * (ncell + 1), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(hmax, 0, sizeof(float) * ncell, s);
@@ -231,7 +241,9 @@ int set_smoothing_impl(trevr_tree* t, const float* h, cudaStream_t s) {
     smoothing_kernel<<<grid_of(n, 256), 256, 0, s>>>(h, t->perm, t->pos, t->w, n, t->sp, t->aw, st);
     note_launch();
     kint_table_kernel<<<grid_of((long long)(kKintNX + 1) * (kKintNS + 1), 256), 256, 0, s>>>(
-        t->kint);
+        tab);
+    note_launch();
+    kint_cells_kernel<<<grid_of((long long)kKintNX * kKintNS, 256), 256, 0, s>>>(tab, t->kint4);
     note_launch();
     for (int L = t->max_depth; L >= 0; --L) {
       const int m = t->h_levels[2 * L + 1] - t->h_levels[2 * L];
@@ -262,15 +274,13 @@ int set_smoothing_impl(trevr_tree* t, const float* h, cudaStream_t s) {
       e = cudaErrorMemoryAllocation;
     } else {
       const size_t m = total > 0 ? total : 1;
-      e = cudaMalloc(&t->nbr, sizeof(int) * m);
+      e = cudaMalloc(&t->nbr_ja, sizeof(int2) * m);
       if (e == cudaSuccess) e = cudaMalloc(&t->nbr_sp, sizeof(float4) * m);
-      if (e == cudaSuccess) e = cudaMalloc(&t->nbr_aw, sizeof(float) * m);
       if (e == cudaSuccess) {
         A.first = t->nbr_first;
-        A.nbr = t->nbr;
         A.aw = t->aw;
+        A.nbr_ja = t->nbr_ja;
         A.nbr_sp = t->nbr_sp;
-        A.nbr_aw = t->nbr_aw;
         nbr_kernel<true><<<grid_of((long long)ncell, 128), 128, 0, s>>>(A);
         note_launch();
         cudaMemcpyAsync(&bad, st, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -280,6 +290,7 @@ int set_smoothing_impl(trevr_tree* t, const float* h, cudaStream_t s) {
     }
   }
   if (hmax) cudaFree(hmax);
+  if (tab) cudaFree(tab);
   if (scratch) cudaFree(scratch);
   if (st) cudaFree(st);
   if (e != cudaSuccess || bad) {
@@ -287,10 +298,9 @@ int set_smoothing_impl(trevr_tree* t, const float* h, cudaStream_t s) {
     free_dev(t->aw);
     free_dev(t->dbk);
     free_dev(t->nbr_first);
-    free_dev(t->nbr);
+    free_dev(t->nbr_ja);
     free_dev(t->nbr_sp);
-    free_dev(t->nbr_aw);
-    free_dev(t->kint);
+    free_dev(t->kint4);
     t->n_nbr = 0;
     if (e == cudaErrorMemoryAllocation) return TREVR_ERR_OUT_OF_MEMORY;
     return e != cudaSuccess ? cuda_to_error(e) : status_to_error(bad);

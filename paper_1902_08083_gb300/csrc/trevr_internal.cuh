@@ -68,10 +68,11 @@ struct TreeView {
   const float* aw;     // per sorted particle alpha * w
   const float* dbk;    // per cell: alpha spread of a leaf's particles
   const unsigned* nbr_first;
-  const int* nbr;
-  const float4* nbr_sp;  // per list entry: the neighbour's (x, y, z, h), contiguous per leaf
-  const float* nbr_aw;   // per list entry: the neighbour's alpha * w
-  const float* kint;   // kernel-integral table, (kKintNX + 1) x (kKintNS + 1), sigma fastest
+  const int2* nbr_ja;    // per list entry: the neighbour's sorted index and alpha * w (bits)
+  const float4* nbr_sp;  // per list entry: the neighbour's (x, y, z, 1/h), contiguous per leaf
+  // kernel-integral table: per cell (i, j) of the kKintNX x kKintNS grid, sigma fastest,
+  // the values at its corners (i, j), (i, j + 1), (i + 1, j), (i + 1, j + 1)
+  const float4* kint4;
 };
 
 }  // namespace trevr
@@ -131,11 +132,11 @@ struct trevr_tree {
   float* aw;         // per sorted particle alpha * w (absorbing mass kappa m)
   float* dbk;        // per cell: max - min of alpha over a leaf's particles (0 inside)
   unsigned* nbr_first;  // per cell + 1: start of the leaf's neighbour list
-  int* nbr;          // sorted particle indices whose kernel support meets the leaf
-  float4* nbr_sp;    // the same entries' (x, y, z, h), so a leaf's list is read coalesced
-  float* nbr_aw;     // the same entries' alpha * w
+  int2* nbr_ja;      // the particles whose kernel support meets the leaf: sorted index and
+                     // alpha * w (float bits)
+  float4* nbr_sp;    // the same entries' (x, y, z, 1/h), so a leaf's list is read coalesced
   long long n_nbr;
-  float* kint;       // kernel-integral table of the sub-bucket trace (see TreeView)
+  float4* kint4;     // kernel-integral table of the sub-bucket trace (see TreeView)
   int h_levels[2 * trevr::kMaxLevels];  // host copy of the level ranges
   // bookkeeping
   int* levels;    // kMaxLevels x 2 (begin, end)

@@ -619,41 +619,31 @@ __device__ __forceinline__ void warp_atomic_add(double* base, int key, float v) 
 // integral of w(sqrt(x + t^2)) over t in [0, sigma]: odd in sigma and constant beyond
 // the support. Phi comes from the tree's pre-computed table (the paper's pre-computed
 // kernel integral), bilinear in (x, sigma).
-__device__ __forceinline__ float kint_phi(const float* __restrict__ tab, float x, float sigma) {
+__device__ __forceinline__ float kint_phi(const float4* __restrict__ tab, float x, float sigma) {
   const float a = fminf(fabsf(sigma), 2.0f);
   const float fx = x * (0.25f * (float)kKintNX), fs = a * (0.5f * (float)kKintNS);
   const int i = min((int)fx, kKintNX - 1), j = min((int)fs, kKintNS - 1);
   const float u = fx - (float)i, v = fs - (float)j;
-  const float* r0 = tab + (size_t)i * (kKintNS + 1) + j;
-  const float* r1 = r0 + (kKintNS + 1);
-  const float p0 = fmaf(v, __ldg(r0 + 1) - __ldg(r0), __ldg(r0));
-  const float p1 = fmaf(v, __ldg(r1 + 1) - __ldg(r1), __ldg(r1));
+  const float4 c = __ldg(tab + (size_t)i * kKintNS + j);  // the cell's four corners
+  const float p0 = fmaf(v, c.y - c.x, c.x);
+  const float p1 = fmaf(v, c.w - c.z, c.z);
   const float p = fmaf(u, p1 - p0, p0);
   return sigma < 0.0f ? -p : p;
 }
 
-// integral of W(sqrt(b^2 + u^2), H) du over [s0, s1]
-__device__ __forceinline__ float kernel_line(const float* __restrict__ tab, float b2, float s0,
-                                             float s1, float H) {
-  const float invh = 1.0f / H;
-  const float x = b2 * invh * invh;
-  if (!(x < 4.0f)) return 0.0f;
-  return (kint_phi(tab, x, s1 * invh) - kint_phi(tab, x, s0 * invh)) *
-         (invh * invh * 0.318309886f);
-}
-
 // Per-warp queue of the neighbours whose support meets the chord, so that the
-// quadrature runs on full warps: (b^2, s0, s1, h) and the absorbing mass.
+// quadrature runs on full warps: (x, sigma_0, sigma_1, alpha w / (pi h^2)).
 struct SubQueue {
   float4 g[64];
-  float a[64];
 };
 
 // Optical depth of lane src's chord p + t d, t in [t0, t1], through the particles
 // listed for its leaf, the receiving particle (sorted index si) left out. The 32
-// lanes of the warp test one neighbour each per round; the neighbours that reach
-// the chord are queued in shared memory and integrated 32 at a time. Every lane
-// must call it; all lanes return the sum.
+// lanes of the warp test one neighbour each per round, with the next round's
+// entries already loading; the neighbours that reach the chord are queued in shared
+// memory and integrated 32 at a time: (Phi(x, sigma_1) - Phi(x, sigma_0)) times
+// alpha w / (pi h^2), with x = b^2 / h^2 and sigma = s / h. Every lane must call it;
+// all lanes return the sum.
 __device__ __forceinline__ float sub_bucket_tau_warp(const TreeView& T, int src, int box, int si,
                                                      float px, float py, float pz, float dx,
                                                      float dy, float dz, float s2, float len,
@@ -678,49 +668,55 @@ __device__ __forceinline__ float sub_bucket_tau_warp(const TreeView& T, int src,
   float part = 0.0f;
   int qn = 0;  // queued entries (warp-uniform)
   const unsigned k0 = __ldg(&T.nbr_first[box]), k1 = __ldg(&T.nbr_first[box + 1]);
+  int2 nja = make_int2(-1, 0);  // the next round's entries
+  float4 nq = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
+  if (k0 + lane < k1) {
+    nja = __ldg(&T.nbr_ja[k0 + lane]);
+    nq = __ldg(&T.nbr_sp[k0 + lane]);
+  }
   for (unsigned base = k0; base < k1; base += 32u) {
     const unsigned k = base + lane;
+    const int2 ja = nja;
+    const float4 q = nq;
+    if (k + 32u < k1) {
+      nja = __ldg(&T.nbr_ja[k + 32u]);
+      nq = __ldg(&T.nbr_sp[k + 32u]);
+    }
+    const float a = __int_as_float(ja.y);
     bool pass = false;
-    float a = 0.0f, b2 = 0.0f, sa = 0.0f, sb = 0.0f, H = 1.0f;
-    if (k < k1) {
-      const int j = __ldg(&T.nbr[k]);
-      a = __ldg(&T.nbr_aw[k]);
-      if (j != si && a > 0.0f) {
-        const float4 q = __ldg(&T.nbr_sp[k]);
-        const float ux = q.x - px, uy = q.y - py, uz = q.z - pz;
-        const float tc = (ux * dx + uy * dy + uz * dz) * inv_s2;
-        const float ex = ux - tc * dx, ey = uy - tc * dy, ez = uz - tc * dz;
-        b2 = ex * ex + ey * ey + ez * ez;
-        H = q.w;
-        sa = (t0 - tc) * len;
-        sb = (t1 - tc) * len;
-        const float R2 = 4.0f * H * H;
-        if (b2 < R2) {  // the chord [sa, sb] must meet the support |s| < u2
-          // sb > -u2 and sa < u2 with u2 = sqrt(R2 - b2) >= 0, compared in squares
-          const float u22 = R2 - b2;
-          pass = (sb > 0.0f || sb * sb < u22) && (sa < 0.0f || sa * sa < u22);
-        }
+    float x = 0.0f, sa = 0.0f, sb = 0.0f;
+    if (k < k1 && ja.x != si && a > 0.0f) {
+      const float ux = q.x - px, uy = q.y - py, uz = q.z - pz;
+      const float tc = (ux * dx + uy * dy + uz * dz) * inv_s2;
+      const float ex = ux - tc * dx, ey = uy - tc * dy, ez = uz - tc * dz;
+      const float b2 = ex * ex + ey * ey + ez * ez;
+      const float ih = q.w;
+      x = b2 * ih * ih;
+      sa = ((t0 - tc) * len) * ih;
+      sb = ((t1 - tc) * len) * ih;
+      if (x < 4.0f) {  // the chord [sa, sb] must meet the support |sigma| < sqrt(4 - x)
+        const float u22 = 4.0f - x;
+        pass = (sb > 0.0f || sb * sb < u22) && (sa < 0.0f || sa * sa < u22);
       }
     }
     const unsigned m = __ballot_sync(FULL, pass);
     if (pass) {
-      const int at = qn + __popc(m & ((1u << lane) - 1u));
-      Q.g[at] = make_float4(b2, sa, sb, H);
-      Q.a[at] = a;
+      const float ih = q.w;
+      Q.g[qn + __popc(m & ((1u << lane) - 1u))] =
+          make_float4(x, sa, sb, a * (ih * ih * 0.318309886f));
     }
     qn += __popc(m);
     __syncwarp();
     if (qn >= 32) {
-      const int at = qn - 32 + (int)lane;
-      const float4 g = Q.g[at];
-      part += Q.a[at] * kernel_line(T.kint, g.x, g.y, g.z, g.w);
+      const float4 g = Q.g[qn - 32 + (int)lane];
+      part += g.w * (kint_phi(T.kint4, g.x, g.z) - kint_phi(T.kint4, g.x, g.y));
       qn -= 32;
       __syncwarp();
     }
   }
   if ((int)lane < qn) {
     const float4 g = Q.g[lane];
-    part += Q.a[lane] * kernel_line(T.kint, g.x, g.y, g.z, g.w);
+    part += g.w * (kint_phi(T.kint4, g.x, g.z) - kint_phi(T.kint4, g.x, g.y));
   }
   __syncwarp();
 #pragma unroll
