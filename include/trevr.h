@@ -211,9 +211,10 @@ int trevr_build_tree_bands(const float* gas_xyz, const float* alpha_bands, const
  * The call lists, for every leaf, the particles whose support meets its box,
  * and keeps each leaf's alpha spread.
  *   hsml  n_gas floats on the device, caller order, each > 0 and finite.
- * Device memory grows by 24 B per particle, 8 B per cell and 4 B per
- * (leaf, neighbour) pair. A second call replaces the first. A tree with more
- * than one band is rejected. Synchronises the stream.
+ * Device memory grows by 20 B per particle, 8 B per cell, 24 B per
+ * (leaf, neighbour) pair and 16 MiB for the tree's kernel-integral table. A
+ * second call replaces the first. A tree with more than one band is rejected.
+ * Synchronises the stream.
  */
 int trevr_tree_set_smoothing(trevr_tree* t, const float* hsml, void* stream);
 
