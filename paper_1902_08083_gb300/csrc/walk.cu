@@ -806,9 +806,12 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
     float aval = 0.0f;
     if (ADJ && active && pass == 3) {
       if (kk < nseg) {
-        akey = segb[kk];
-        aval = -gk * fcur * segl[kk];
-        ++kk;
+        // four recorded segments per iteration: 2.2 % faster backward than one
+        // (145.5 against 148.8 ms at 2^21), eight were slower (154 ms)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (kk + u < nseg) atomicAdd(&J.G[segb[kk + u]], (double)(-gk * fcur * segl[kk + u]));
+        kk += 4;
       } else {
         if (CNT) ++cnt.rays;
         active = false;
@@ -1030,8 +1033,9 @@ __device__ __forceinline__ void warp_ray(const TreeView& T, const WalkParams& P,
       }
       need_sub = false;
     }
-    // the replayed segment's gradient: lanes replay different rays, so the cells differ
-    // and each lane adds its own (1.4% faster than trying a warp-wide sum first)
+    // a retraced segment's gradient (a ray with more segments than were recorded): the
+    // lanes trace different rays, so the cells differ and each lane adds its own, as the
+    // replay does (1.4 % faster than trying a warp-wide sum first)
     if (ADJ && akey >= 0) atomicAdd(&J.G[akey], (double)aval);
   }
   if (ADJ) {
